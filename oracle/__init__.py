@@ -1,0 +1,274 @@
+"""FP64 CPU oracle for DFacTo -- test infrastructure only.
+
+This package wraps ``dfacto_oracle.c`` (a plain, slow, FP64 restatement of the
+paper's MTTKRP, CSR construction, ALS, GD and fit) with ctypes + numpy.  Only the
+tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may import
+it.  The CUDA library never imports, links or calls anything in here, and nothing
+here imports the library: the two share no code.
+
+Every array crossing into C is converted to a C-contiguous numpy array of the
+stated dtype; factor matrices are float64, row-major (rows x R).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dfacto_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+OK, EINVAL, ERANGE, EDUP, ENOMEM, ESINGULAR, ELSFAIL = 0, 1, 2, 3, 4, 6, 7
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into oracle/liboracle.so (if stale)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        # DFACTO_ORACLE_LIB points the wrapper at another build of the same source
+        # (the mutation tests load deliberately broken copies this way).
+        path = os.environ.get("DFACTO_ORACLE_LIB")
+        if not path:
+            path = build()
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        I64 = ctypes.c_int64
+        I32 = ctypes.c_int
+        D = ctypes.c_double
+        sig = {
+            "orc_check_coo": (I32, [I64, P, P]),
+            "orc_build_csr": (I32, [I32, I64, P, P, P, P, P, P, P, P, P]),
+            "orc_mttkrp": (None, [I32, I64, P, P, P, I32, P, P, P, P]),
+            "orc_mttkrp_rows": (I32, [I32, I64, P, P, P, I32, P, P, P, I64, P, P]),
+            "orc_gram": (None, [I64, I32, P, P]),
+            "orc_sym_eig_jacobi": (I32, [I32, P, P, P]),
+            "orc_pinv_sym": (I32, [I32, P, P]),
+            "orc_solve_normal": (I32, [I64, I32, P, P, P]),
+            "orc_als_mode_update": (I32, [I32, I64, P, P, P, I32, D, P, P, P, P]),
+            "orc_als_sweep": (I32, [I64, P, P, P, I32, D, P, P, P, P, P]),
+            "orc_norm2": (D, [I64, P]),
+            "orc_inner": (D, [I64, P, P, I32, P, P, P, P]),
+            "orc_model_norm2": (D, [P, I32, P, P, P, P]),
+            "orc_fit": (D, [I64, P, P, P, I32, P, P, P, P]),
+            "orc_loss": (D, [I64, P, P, P, I32, D, P, P, P]),
+            "orc_gd_gradient": (I32, [I64, P, P, P, I32, D, P, P, P, P, P, P]),
+            "orc_gd_step": (I32, [I64, P, P, P, I32, D, P, P, P, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Tensor:
+    """A COO tensor as the oracle sees it: idx int32[3, nnz], val float32[nnz]."""
+
+    def __init__(self, idx, val, dims: Sequence[int]):
+        self.idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int32).reshape(3, -1))
+        self.val = np.ascontiguousarray(np.asarray(val, dtype=np.float32).reshape(-1))
+        self.dims = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(3))
+        self.nnz = int(self.val.shape[0])
+        assert self.idx.shape[1] == self.nnz
+
+
+def _f64(a, rows: int, R: int) -> np.ndarray:
+    out = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    assert out.shape == (rows, R), (out.shape, rows, R)
+    return out
+
+
+def axes(mode: int) -> Tuple[int, int, int]:
+    """(o, in, f) axes of mode n: o = n, in = n+1, f = n+2 (mod 3)."""
+    return mode, (mode + 1) % 3, (mode + 2) % 3
+
+
+def check_coo(t: Tensor) -> int:
+    return _load().orc_check_coo(t.nnz, _p(t.idx), _p(t.dims))
+
+
+def build_csr(t: Tensor, mode: int):
+    """Return (status, dict of CSR arrays) for mode 0, 1 or 2."""
+    lib = _load()
+    o = mode
+    n = max(t.nnz, 1)
+    fiber_ptr = np.zeros(int(t.dims[o]) + 1, np.int64)
+    fiber_idx = np.zeros(n, np.int32)
+    nz_ptr = np.zeros(n + 1, np.int64)
+    nz_idx = np.zeros(n, np.int32)
+    nz_val = np.zeros(n, np.float32)
+    nfib = np.zeros(1, np.int64)
+    st = lib.orc_build_csr(mode, t.nnz, _p(t.idx), _p(t.val), _p(t.dims), _p(fiber_ptr),
+                           _p(fiber_idx), _p(nz_ptr), _p(nz_idx), _p(nz_val), _p(nfib))
+    if st != OK:
+        return st, None
+    nf = int(nfib[0])
+    return st, dict(fiber_ptr=fiber_ptr, fiber_idx=fiber_idx[:nf].copy(),
+                    nz_ptr=nz_ptr[:nf + 1].copy(), nz_idx=nz_idx[:t.nnz].copy(),
+                    nz_val=nz_val[:t.nnz].copy(), nfib=nf)
+
+
+def mttkrp(t: Tensor, mode: int, factors: Sequence[np.ndarray]) -> np.ndarray:
+    R = int(np.asarray(factors[0]).shape[1])
+    F = [_f64(factors[m], int(t.dims[m]), R) for m in range(3)]
+    out = np.zeros((int(t.dims[mode]), R), np.float64)
+    _load().orc_mttkrp(mode, t.nnz, _p(t.idx), _p(t.val), _p(t.dims), R,
+                       _p(F[0]), _p(F[1]), _p(F[2]), _p(out))
+    return out
+
+
+def mttkrp_rows(t: Tensor, mode: int, factors: Sequence[np.ndarray], rows) -> np.ndarray:
+    R = int(np.asarray(factors[0]).shape[1])
+    F = [_f64(factors[m], int(t.dims[m]), R) for m in range(3)]
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    out = np.zeros((rows.shape[0], R), np.float64)
+    st = _load().orc_mttkrp_rows(mode, t.nnz, _p(t.idx), _p(t.val), _p(t.dims), R,
+                                 _p(F[0]), _p(F[1]), _p(F[2]), rows.shape[0], _p(rows),
+                                 _p(out))
+    if st != OK:
+        raise ValueError("orc_mttkrp_rows status %d" % st)
+    return out
+
+
+def gram(F: np.ndarray) -> np.ndarray:
+    F = np.ascontiguousarray(np.asarray(F, dtype=np.float64))
+    R = F.shape[1]
+    G = np.zeros((R, R), np.float64)
+    _load().orc_gram(F.shape[0], R, _p(F), _p(G))
+    return G
+
+
+def sym_eig_jacobi(S: np.ndarray):
+    A = np.ascontiguousarray(np.array(S, dtype=np.float64))
+    R = A.shape[0]
+    V = np.zeros((R, R), np.float64)
+    w = np.zeros(R, np.float64)
+    _load().orc_sym_eig_jacobi(R, _p(A), _p(V), _p(w))
+    return w, V
+
+
+def pinv_sym(S: np.ndarray) -> np.ndarray:
+    S = np.ascontiguousarray(np.asarray(S, dtype=np.float64))
+    P = np.zeros_like(S)
+    _load().orc_pinv_sym(S.shape[0], _p(S), _p(P))
+    return P
+
+
+def solve_normal(Gamma: np.ndarray, N: np.ndarray):
+    Gamma = np.ascontiguousarray(np.asarray(Gamma, dtype=np.float64))
+    N = np.ascontiguousarray(np.asarray(N, dtype=np.float64))
+    X = np.zeros_like(N)
+    st = _load().orc_solve_normal(N.shape[0], N.shape[1], _p(Gamma), _p(N), _p(X))
+    return st, X
+
+
+def _factors_rw(t: Tensor, factors):
+    R = int(np.asarray(factors[0]).shape[1])
+    return R, [np.array(_f64(factors[m], int(t.dims[m]), R)) for m in range(3)]
+
+
+def als_mode_update(t: Tensor, mode: int, factors, lambda_reg: float = 0.0):
+    """Returns (status, [A,B,C] updated copies, lambda)."""
+    R, F = _factors_rw(t, factors)
+    lam = np.zeros(R, np.float64)
+    st = _load().orc_als_mode_update(mode, t.nnz, _p(t.idx), _p(t.val), _p(t.dims), R,
+                                     float(lambda_reg), _p(F[0]), _p(F[1]), _p(F[2]),
+                                     _p(lam))
+    return st, F, lam
+
+
+def als_sweep(t: Tensor, factors, lambda_reg: float = 0.0):
+    """Returns (status, [A,B,C] updated copies, lambda, fit)."""
+    R, F = _factors_rw(t, factors)
+    lam = np.zeros(R, np.float64)
+    fit = np.zeros(1, np.float64)
+    st = _load().orc_als_sweep(t.nnz, _p(t.idx), _p(t.val), _p(t.dims), R,
+                               float(lambda_reg), _p(F[0]), _p(F[1]), _p(F[2]), _p(lam),
+                               _p(fit))
+    return st, F, lam, float(fit[0])
+
+
+def norm2(t: Tensor) -> float:
+    return _load().orc_norm2(t.nnz, _p(t.val))
+
+
+def inner(t: Tensor, factors, lam=None) -> float:
+    R = int(np.asarray(factors[0]).shape[1])
+    F = [_f64(factors[m], int(t.dims[m]), R) for m in range(3)]
+    lam = None if lam is None else np.ascontiguousarray(np.asarray(lam, np.float64))
+    return _load().orc_inner(t.nnz, _p(t.idx), _p(t.val), R, _p(lam), _p(F[0]), _p(F[1]),
+                             _p(F[2]))
+
+
+def model_norm2(dims, factors, lam=None) -> float:
+    R = int(np.asarray(factors[0]).shape[1])
+    dims = np.ascontiguousarray(np.asarray(dims, np.int32))
+    F = [_f64(factors[m], int(dims[m]), R) for m in range(3)]
+    lam = None if lam is None else np.ascontiguousarray(np.asarray(lam, np.float64))
+    return _load().orc_model_norm2(_p(dims), R, _p(lam), _p(F[0]), _p(F[1]), _p(F[2]))
+
+
+def fit(t: Tensor, factors, lam=None) -> float:
+    R = int(np.asarray(factors[0]).shape[1])
+    F = [_f64(factors[m], int(t.dims[m]), R) for m in range(3)]
+    lam = None if lam is None else np.ascontiguousarray(np.asarray(lam, np.float64))
+    return _load().orc_fit(t.nnz, _p(t.idx), _p(t.val), _p(t.dims), R, _p(lam), _p(F[0]),
+                           _p(F[1]), _p(F[2]))
+
+
+def loss(t: Tensor, factors, lambda_reg: float = 0.0) -> float:
+    R = int(np.asarray(factors[0]).shape[1])
+    F = [_f64(factors[m], int(t.dims[m]), R) for m in range(3)]
+    return _load().orc_loss(t.nnz, _p(t.idx), _p(t.val), _p(t.dims), R, float(lambda_reg),
+                            _p(F[0]), _p(F[1]), _p(F[2]))
+
+
+def gd_gradient(t: Tensor, factors, lambda_reg: float = 0.0):
+    R = int(np.asarray(factors[0]).shape[1])
+    F = [_f64(factors[m], int(t.dims[m]), R) for m in range(3)]
+    G = [np.zeros_like(F[m]) for m in range(3)]
+    st = _load().orc_gd_gradient(t.nnz, _p(t.idx), _p(t.val), _p(t.dims), R,
+                                 float(lambda_reg), _p(F[0]), _p(F[1]), _p(F[2]), _p(G[0]),
+                                 _p(G[1]), _p(G[2]))
+    if st != OK:
+        raise MemoryError("orc_gd_gradient status %d" % st)
+    return G
+
+
+def gd_step(t: Tensor, factors, alpha_prev: float = 0.0, lambda_reg: float = 0.0):
+    """Returns (status, [A,B,C] updated copies, alpha, loss, g2)."""
+    R, F = _factors_rw(t, factors)
+    a = np.array([alpha_prev], np.float64)
+    lo = np.zeros(1, np.float64)
+    g2 = np.zeros(1, np.float64)
+    st = _load().orc_gd_step(t.nnz, _p(t.idx), _p(t.val), _p(t.dims), R, float(lambda_reg),
+                             _p(F[0]), _p(F[1]), _p(F[2]), _p(a), _p(lo), _p(g2))
+    return st, F, float(a[0]), float(lo[0]), float(g2[0])
+
+
+if __name__ == "__main__":  # pragma: no cover
+    print(build(force="--force" in sys.argv))

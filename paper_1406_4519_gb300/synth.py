@@ -1,0 +1,205 @@
+"""Seeded synthetic sparse 3-way tensors and factor initialisations.
+
+This module only draws inputs: coordinates, values and starting factors.  It
+contains none of the factorization's arithmetic and imports nothing else from
+this package, so both the CUDA library's tests and the CPU oracle can be fed
+from it.  Everything runs in plain PyTorch on the device it is asked for
+(``cpu`` or ``cuda``); a given (recipe, seed, device) always yields the same
+tensor.
+
+Recipes (the shapes and distributions of the workloads this library is
+measured on; the paper's real datasets are not available, these stand in):
+
+* ``uniform_tensor``  -- unique coordinates drawn uniformly, values U(0,1).
+* ``zipf_tensor``     -- per-mode Zipf(s) coordinates (index 0 the most
+  frequent), deduplicated to exactly ``nnz`` unique coordinates by redrawing;
+  values either a planted CP model plus Gaussian noise, lognormal(0,1) or U(0,1).
+* ``normal_factors``  -- N(0,1) starting factors.
+
+Coordinates are returned as int32 [3, nnz] (rows i, j, k), values as float32,
+in a seeded random order (never pre-sorted).
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Optional, Sequence, Tuple
+
+import torch
+
+__all__ = [
+    "generator", "zipf_cdf", "draw_zipf", "unique_coords", "uniform_tensor",
+    "zipf_tensor", "normal_factors", "batch_job_specs", "poisson_arrivals",
+]
+
+
+def generator(seed: int, device) -> torch.Generator:
+    g = torch.Generator(device=torch.device(device))
+    g.manual_seed(int(seed) & ((1 << 63) - 1))
+    return g
+
+
+def zipf_cdf(n: int, s: float) -> torch.Tensor:
+    """CDF table of Zipf(s) truncated to ranks 1..n, as float64 on the CPU.
+
+    Rank r has probability proportional to r**-s; rank r maps to index r-1.
+    """
+    w = torch.arange(1, n + 1, dtype=torch.float64).pow_(-float(s))
+    c = torch.cumsum(w, 0)
+    c /= c[-1].clone()
+    c[-1] = 1.0
+    return c
+
+
+def draw_zipf(m: int, cdf: torch.Tensor, g: torch.Generator, device) -> torch.Tensor:
+    u = torch.rand(m, dtype=torch.float64, generator=g, device=device)
+    idx = torch.searchsorted(cdf, u, right=True)
+    return idx.clamp_(max=cdf.numel() - 1)
+
+
+def _first_occurrences(cols: List[torch.Tensor]) -> torch.Tensor:
+    """Positions (ascending) of the first occurrence of each distinct tuple.
+
+    ``cols`` are int64 key columns, most significant first; the tuple order is
+    found with stable sorts from the least significant column up.
+    """
+    n = cols[0].numel()
+    order = torch.arange(n, device=cols[0].device)
+    for c in reversed(cols):
+        order = order[torch.argsort(c[order], stable=True)]
+    first = torch.ones(n, dtype=torch.bool, device=cols[0].device)
+    if n > 1:
+        diff = torch.zeros(n - 1, dtype=torch.bool, device=cols[0].device)
+        for c in cols:
+            sc = c[order]
+            diff |= sc[1:] != sc[:-1]
+        first[1:] = diff
+    return torch.sort(order[first]).values
+
+
+def _key_columns(ijk: torch.Tensor, dims: Sequence[int]) -> List[torch.Tensor]:
+    I, J, K = (int(d) for d in dims)
+    if I * J * K < (1 << 62):
+        return [(ijk[0] * J + ijk[1]) * K + ijk[2]]
+    return [ijk[0], ijk[1] * K + ijk[2]]
+
+
+def unique_coords(dims: Sequence[int], nnz: int, sampler, g: torch.Generator, device,
+                  max_rounds: int = 400) -> torch.Tensor:
+    """Draw coordinates with ``sampler(m) -> int64 [3, m]`` until ``nnz`` are unique.
+
+    Duplicates are redrawn from the same distribution; the first ``nnz`` distinct
+    coordinates in draw order are kept.  Returns int64 [3, nnz].
+    """
+    cap = int(dims[0]) * int(dims[1]) * int(dims[2])
+    if nnz > cap:
+        raise ValueError("nnz %d exceeds the %d cells of the tensor" % (nnz, cap))
+    pool = torch.empty((3, 0), dtype=torch.int64, device=device)
+    for _ in range(max_rounds):
+        need = nnz - pool.shape[1]
+        if need <= 0:
+            break
+        m = int(need * 1.05) + 64
+        pool = torch.cat([pool, sampler(m)], dim=1)
+        keep = _first_occurrences(_key_columns(pool, dims))
+        pool = pool[:, keep]
+    if pool.shape[1] < nnz:
+        raise RuntimeError("could not draw %d unique coordinates" % nnz)
+    return pool[:, :nnz]
+
+
+def _shuffle(ijk: torch.Tensor, g: torch.Generator, device) -> torch.Tensor:
+    perm = torch.randperm(ijk.shape[1], generator=g, device=device)
+    return ijk[:, perm]
+
+
+def uniform_tensor(dims: Sequence[int], nnz: int, seed: int, device="cpu"
+                   ) -> Tuple[torch.Tensor, torch.Tensor]:
+    """Unique uniform coordinates, values U(0,1)."""
+    device = torch.device(device)
+    g = generator(seed, device)
+
+    def sampler(m):
+        return torch.stack([torch.randint(0, int(d), (m,), generator=g, device=device)
+                            for d in dims])
+
+    ijk = _shuffle(unique_coords(dims, nnz, sampler, g, device), g, device)
+    val = torch.rand(nnz, generator=g, device=device, dtype=torch.float32)
+    return ijk.to(torch.int32).contiguous(), val.contiguous()
+
+
+def normal_factors(dims: Sequence[int], R: int, seed: int, device="cpu",
+                   dtype=torch.float32) -> List[torch.Tensor]:
+    """Three N(0,1) factor matrices dims[m] x R (row-major)."""
+    device = torch.device(device)
+    g = generator(seed, device)
+    return [torch.randn(int(d), R, generator=g, device=device, dtype=torch.float64)
+            .to(dtype).contiguous() for d in dims]
+
+
+def zipf_tensor(dims: Sequence[int], nnz: int, exponents: Sequence[float], seed: int,
+                device="cpu", values: str = "cp", R_true: int = 32,
+                noise: float = 0.01, chunk: int = 1 << 22
+                ) -> Tuple[torch.Tensor, torch.Tensor]:
+    """Per-mode Zipf coordinates, exactly ``nnz`` unique.
+
+    values = "cp":        x = sum_r a_ir b_jr c_kr over planted N(0,1) factors of
+                          rank ``R_true``, plus N(0, (noise * rms(x))^2);
+             "lognormal": x = exp(N(0,1));
+             "uniform":   x ~ U(0,1).
+    """
+    device = torch.device(device)
+    g = generator(seed, device)
+    cdfs = [zipf_cdf(int(d), s).to(device) for d, s in zip(dims, exponents)]
+
+    def sampler(m):
+        return torch.stack([draw_zipf(m, c, g, device) for c in cdfs])
+
+    ijk = _shuffle(unique_coords(dims, nnz, sampler, g, device), g, device)
+    if values == "cp":
+        gp = generator(seed + 7919, device)
+        planted = [torch.randn(int(d), R_true, generator=gp, device=device,
+                               dtype=torch.float64) for d in dims]
+        x = torch.empty(nnz, dtype=torch.float64, device=device)
+        for s0 in range(0, nnz, chunk):
+            s1 = min(nnz, s0 + chunk)
+            x[s0:s1] = (planted[0][ijk[0, s0:s1]] * planted[1][ijk[1, s0:s1]]
+                        * planted[2][ijk[2, s0:s1]]).sum(1)
+        rms = float(torch.sqrt(torch.mean(x * x))) if nnz else 0.0
+        x += noise * rms * torch.randn(nnz, generator=g, device=device, dtype=torch.float64)
+        val = x.to(torch.float32)
+    elif values == "lognormal":
+        val = torch.exp(torch.randn(nnz, generator=g, device=device, dtype=torch.float64)
+                        ).to(torch.float32)
+    elif values == "uniform":
+        val = torch.rand(nnz, generator=g, device=device, dtype=torch.float32)
+    else:
+        raise ValueError(values)
+    return ijk.to(torch.int32).contiguous(), val.contiguous()
+
+
+def batch_job_specs(n_jobs: int, seed: int, dim_lo: int = 1000, dim_hi: int = 200000,
+                    nnz_median: float = 5e5, nnz_sigma: float = 1.0, nnz_lo: int = 10000,
+                    nnz_hi: int = 5000000, ranks: Sequence[int] = (8, 16, 32)):
+    """Shapes of independent jobs: dims log-uniform in [dim_lo, dim_hi], nnz
+    lognormal with the given median and sigma clipped to [nnz_lo, nnz_hi], R
+    uniform over ``ranks``.  Returns a list of dicts (dims, nnz, R, seed)."""
+    g = generator(seed, "cpu")
+    specs = []
+    for t in range(n_jobs):
+        u = torch.rand(3, generator=g, dtype=torch.float64)
+        dims = [int(round(math.exp(math.log(dim_lo) + float(x) *
+                                   (math.log(dim_hi) - math.log(dim_lo))))) for x in u]
+        z = float(torch.randn(1, generator=g, dtype=torch.float64))
+        nnz = int(min(max(math.exp(math.log(nnz_median) + nnz_sigma * z), nnz_lo), nnz_hi))
+        nnz = min(nnz, dims[0] * dims[1] * dims[2] // 2)
+        R = int(ranks[int(torch.randint(0, len(ranks), (1,), generator=g))])
+        specs.append(dict(dims=dims, nnz=nnz, R=R, seed=int(seed * 1000003 + t)))
+    return specs
+
+
+def poisson_arrivals(n: int, rate_per_s: float, seed: int) -> List[float]:
+    """Arrival times (seconds from 0) of a Poisson process of the given rate."""
+    g = generator(seed, "cpu")
+    u = torch.rand(n, generator=g, dtype=torch.float64).clamp_(min=1e-300)
+    gaps = -torch.log(u) / float(rate_per_s)
+    return torch.cumsum(gaps, 0).tolist()
