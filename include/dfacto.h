@@ -1,0 +1,241 @@
+/*
+ * dfacto.h -- C ABI of libdfacto, a GB300 (sm_103a) implementation of DFacTo
+ * (Choi & Vishwanathan, "DFacTo: Distributed Factorization of Tensors",
+ * NIPS 2014): CP decomposition of sparse 3-way tensors by ALS and GD, with the
+ * matricized-tensor times Khatri-Rao product (MTTKRP) computed as the paper's two
+ * sparse matrix-vector products over flattened CSR copies of the tensor, batched
+ * across all R columns.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  - Indices are 0-based.  A tensor X is I x J x K = dims[0] x dims[1] x dims[2].
+ *  - "Mode" n is 0, 1 or 2 and names the factor being solved for: mode 0 is
+ *    N = X^1 (C kr B) (updates A), mode 1 is X^2 (A kr C) (updates B), mode 2 is
+ *    X^3 (B kr A) (updates C), with the flattenings of Eq. x1 and the operand
+ *    order of Algorithm 4.  For mode n the CSR copy pairs rows (o, f) with
+ *    entries `in`, where o = n, in = (n+1) mod 3, f = (n+2) mod 3.
+ *  - Factor matrices are row-major: row t of F_m holds F_m[t, 0..R-1].
+ *  - Pointers may be host or device memory unless a function says otherwise;
+ *    the library finds out with cudaPointerGetAttributes.  Device pointers must
+ *    be 16-byte aligned.  The caller keeps ownership of every buffer it passes;
+ *    the library never keeps a caller pointer after the call returns.
+ *  - Work is queued on the handle's stream.  Functions that return a host value
+ *    (fit, loss, lambda, CSR sizes) synchronize that stream; the others do not.
+ *  - Every function returns a status and never aborts the process.  After
+ *    DFACTO_ECUDA the handle must be destroyed.  dfacto_last_error() gives a
+ *    one-line description of the last failure on a handle.
+ *  - Calls on one handle are not thread-safe; distinct handles are independent.
+ */
+#ifndef DFACTO_H_
+#define DFACTO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dfacto_status {
+  DFACTO_OK = 0,
+  DFACTO_EINVAL = 1,    /* bad argument (null pointer, mode, rank, sizes)         */
+  DFACTO_ERANGE = 2,    /* a coordinate lies outside dims                         */
+  DFACTO_EDUP = 3,      /* two nonzeros share a coordinate                        */
+  DFACTO_ENOMEM = 4,    /* device (or pinned host) allocation failed              */
+  DFACTO_ECUDA = 5,     /* a CUDA call failed; the handle is unusable             */
+  DFACTO_ESINGULAR = 6, /* informational: a Gram-Hadamard matrix was not positive
+                           definite and its pseudo-inverse was used              */
+  DFACTO_ELSFAIL = 7,   /* GD line search found no acceptable step; the factors
+                           are unchanged                                          */
+  DFACTO_ETIMEOUT = 8,  /* a bounded device-side wait gave up                     */
+  DFACTO_EINTERNAL = 9  /* an internal consistency check failed                   */
+} dfacto_status;
+
+typedef enum dfacto_dtype {
+  DFACTO_F32 = 0,  /* float                                  */
+  DFACTO_BF16 = 1, /* bfloat16 (round-to-nearest-even stores) */
+  DFACTO_F64 = 2   /* double (set/get of factors only)        */
+} dfacto_dtype;
+
+/*
+ * Build and solver options.  Initialise with dfacto_options_init().
+ *   rank          R, 1..128 (R > 32 must be a multiple of 4).
+ *   factor_dtype  storage of A, B, C on the device: DFACTO_F32 or DFACTO_BF16.
+ *                 Products are always accumulated in FP32; Grams, the R x R
+ *                 solves, line-search and fit scalars in FP64.
+ *   lambda_reg    ridge term added to every Gram-Hadamard matrix (ALS) and to
+ *                 the objective (GD): the regularized forms of Appendix B
+ *                 (Eq. tensorapprx-ref-sol) and Appendix C (Eq. gd-obj-fn-reg).
+ *                 Must be >= 0; 0 (the default) is the plain method.
+ *   seg_nnz       nonzeros walked by one lane group in the MTTKRP kernel; 0
+ *                 lets the library choose.  Rounded to a multiple of 32.
+ *   vec           factor columns per lane in the MTTKRP kernel (1, 2, 4 or 8;
+ *                 must divide R); 0 lets the library choose.
+ */
+typedef struct dfacto_options {
+  int32_t rank;
+  int32_t factor_dtype;
+  double lambda_reg;
+  int32_t seg_nnz;
+  int32_t vec;
+  int32_t reserved[6];
+} dfacto_options;
+
+/* Sizes of a built tensor. */
+typedef struct dfacto_info {
+  int32_t dims[3];
+  int32_t rank;
+  int64_t nnz;
+  int64_t nfib[3];       /* fibers (= nnzc of the paired flattening) per mode */
+  int64_t device_bytes;  /* device memory held by the handle                  */
+  double norm_x2;        /* ||X||^2 in FP64                                    */
+  int32_t factor_dtype;
+  int32_t seg_nnz[3];    /* MTTKRP segment length in use per mode              */
+  int32_t vec[3];        /* MTTKRP columns per lane in use per mode            */
+} dfacto_info;
+
+/*
+ * Device pointers to the flattened CSR copy of one mode (Sec. 3, Lemma 3 and
+ * Lemma 4).  For mode n:
+ *   fiber_ptr[dim_o + 1]  row(M^r): the fibers of output row o are
+ *                         fiber_ptr[o] .. fiber_ptr[o+1]-1 (empty rows kept)
+ *   fiber_idx[nfib]       col(M^r): the index f of each fiber
+ *   nz_ptr[nfib + 1]      row pointer of (Xhat^{n+1})^T: fiber q holds the
+ *                         nonzeros nz_ptr[q] .. nz_ptr[q+1]-1
+ *   nz_idx[nnz], nz_val[nnz]  column (index `in`) and value of each nonzero
+ * Fibers are the distinct (o, f) pairs in lexicographic order, entries ascend
+ * in `in` within a fiber.  The arrays belong to the handle and stay valid until
+ * dfacto_destroy().
+ */
+typedef struct dfacto_csr_view {
+  int64_t dim_o;
+  int64_t nfib;
+  int64_t nnz;
+  const int64_t* fiber_ptr;
+  const int32_t* fiber_idx;
+  const int64_t* nz_ptr;
+  const int32_t* nz_idx;
+  const float* nz_val;
+} dfacto_csr_view;
+
+typedef struct dfacto_handle dfacto_t;
+
+/* Fill *opt with the defaults for rank R (FP32 factors, lambda_reg 0, tuned). */
+void dfacto_options_init(dfacto_options* opt, int32_t rank);
+
+/* Static string for a status code. */
+const char* dfacto_status_str(dfacto_status s);
+
+/*
+ * dfacto_build -- validate a COO tensor and build its three flattened CSR
+ * copies on the device (the (Xhat^2)^T, (Xhat^3)^T, (Xhat^1)^T of Sec. 3 with
+ * the fixed sparsity pattern of M^r, Lemma 4), by a radix sort per mode.
+ *   idx     int32[3][nnz], structure of arrays: idx[m*nnz + t] is coordinate m
+ *           of nonzero t.  Host or device.
+ *   val     float[nnz], host or device.  Explicit zeros are kept as observed
+ *           entries (the observed set of Sec. 2).
+ *   nnz     0 <= nnz < 2^31.
+ *   dims    host int32[3], each >= 1.
+ *   opt     build options (rank, factor storage, ...); NULL means rank 1.
+ *   stream  cudaStream_t the handle will use for all its work (NULL: the
+ *           legacy default stream).
+ *   out     receives the new handle.  The handle owns all device memory it
+ *           allocates.  Factors start at zero: set them before solving.
+ * Errors: EINVAL (null pointers, dims < 1, bad rank/options), ERANGE (a
+ * coordinate outside dims), EDUP (repeated coordinate), ENOMEM, ECUDA.  On error
+ * *out is NULL.
+ */
+dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz,
+                           const int32_t dims[3], const dfacto_options* opt, void* stream,
+                           dfacto_t** out);
+
+/* Release every resource of the handle (NULL is allowed). */
+void dfacto_destroy(dfacto_t* h);
+
+/* One-line description of the last failure on the handle ("" if none). */
+const char* dfacto_last_error(const dfacto_t* h);
+
+/* Sizes of the built tensor (host struct). */
+dfacto_status dfacto_get_info(dfacto_t* h, dfacto_info* info);
+
+/* Change the stream used by later calls on this handle. */
+dfacto_status dfacto_set_stream(dfacto_t* h, void* stream);
+
+/* Wait for all work queued on the handle's stream. */
+dfacto_status dfacto_sync(dfacto_t* h);
+
+/*
+ * dfacto_set_factors / dfacto_get_factors -- copy factor matrix `mode`
+ * (dims[mode] x R, row-major) in or out, converting between `dtype` and the
+ * handle's storage type (BF16 storage rounds to nearest even).  The
+ * initialization is the caller's (the paper leaves it open, Algorithm 2).
+ * Setting a factor invalidates its cached Gram.  Host or device buffers.
+ */
+dfacto_status dfacto_set_factors(dfacto_t* h, int mode, const void* F, dfacto_dtype dtype);
+dfacto_status dfacto_get_factors(dfacto_t* h, int mode, void* F, dfacto_dtype dtype);
+
+/*
+ * CP weights lambda_r of Eq. parafac (host double[R]).  ALS writes them (the
+ * column norms of the last updated factor); they are 1 after dfacto_build and
+ * the GD model ignores them.
+ */
+dfacto_status dfacto_get_lambda(dfacto_t* h, double* lambda);
+dfacto_status dfacto_set_lambda(dfacto_t* h, const double* lambda);
+
+/*
+ * dfacto_mttkrp -- N = X^n (F_f kr F_in) for the current factors (Algorithm 1,
+ * Lemma 2): for every column r, value(M^r) <- (Xhat^{n+1})^T F_in[:, r] and
+ * N[:, r] <- M^r F_f[:, r], all R columns in one pass, the intermediate M^r
+ * held in registers only.
+ *   out  device float[dims[mode] x R], row-major, caller-owned; every entry is
+ *        written (rows with no nonzeros get 0).
+ * Asynchronous.  Errors: EINVAL, ECUDA.
+ */
+dfacto_status dfacto_mttkrp(dfacto_t* h, int mode, float* out);
+
+/*
+ * dfacto_als_iter -- one DFacTo-ALS sweep (Algorithm 4 with Algorithm 2):
+ * for modes 0, 1, 2 in turn, N = MTTKRP(mode), Gamma = Gram(F_f) * Gram(F_in)
+ * (+ lambda_reg I) (Eq. kr-product), F_mode = N Gamma^{-1} by Cholesky (the
+ * pseudo-inverse of Eq. kr-pseudo when Gamma is not positive definite), then
+ * column normalisation with lambda = the column 2-norms.  Afterwards the fit
+ * 1 - ||X - [[lambda; A,B,C]]|| / ||X|| is computed in FP64.
+ *   fit_out  host double, nullable.  When NULL nothing is read back and the
+ *            call does not synchronize.
+ * Returns DFACTO_ESINGULAR (after completing the sweep) if a pseudo-inverse was
+ * needed; that status is only seen when fit_out is non-NULL.
+ */
+dfacto_status dfacto_als_iter(dfacto_t* h, double* fit_out);
+
+/*
+ * dfacto_gd_iter -- one DFacTo-GD step (Algorithm 5, with the gradient sign of
+ * Eq. gd-A): the three gradients dF_n = -N_n + F_n Gamma_n (+ lambda_reg F_n) at
+ * the current point, then a backtracking line search -- alpha0 = min(2
+ * alpha_prev, 1) (1 on the first step), accept the first alpha with
+ * f(theta - alpha grad) <= f(theta) - 1e-4 alpha ||grad||^2, halving at most 40
+ * times -- and the update theta <- theta - alpha grad.  f is the objective of
+ * Eq. gd-obj-fn (regularized: Eq. gd-obj-fn-reg), evaluated in FP64.
+ *   loss_out, alpha_out  host doubles, nullable; when both are NULL the call
+ *                        does not synchronize.  loss_out gets f at the returned
+ *                        point, alpha_out the accepted step.
+ * Returns DFACTO_ELSFAIL (factors unchanged) when no trial is accepted; that
+ * status is only seen when an output pointer is non-NULL.
+ */
+dfacto_status dfacto_gd_iter(dfacto_t* h, double* loss_out, double* alpha_out);
+
+/*
+ * dfacto_fit -- fit of the current model [[lambda; A,B,C]]:
+ * 1 - sqrt(max(0, ||X||^2 - 2<X, Xhat> + ||Xhat||^2)) / ||X||, all in FP64, with
+ * <X, Xhat> by one pass over the nonzeros and ||Xhat||^2 = lambda^T (A^T A *
+ * B^T B * C^T C) lambda.  Synchronizes.
+ */
+dfacto_status dfacto_fit(dfacto_t* h, double* fit_out);
+
+/* Device pointers to the CSR copy of one mode (see dfacto_csr_view). */
+dfacto_status dfacto_get_csr(dfacto_t* h, int mode, dfacto_csr_view* view);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFACTO_H_ */

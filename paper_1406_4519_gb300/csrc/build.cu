@@ -1,0 +1,461 @@
+// build.cu -- COO -> flattened CSR copies on the device (Sec. 3, Lemmas 3-4).
+//
+// For each mode n the nonzeros are sorted by the key (o, f, in), o = axis n,
+// f = axis n+2, in = axis n+1: this is the row order of (X^{n+1})^T (row index
+// f + o*dim_f in 0-based form of the proof of Lemma 4) with ascending columns
+// inside each row.  Maximal runs of equal (o, f) are the nonzero rows of
+// (X^{n+1})^T, i.e. the fibers; their starts give nz_ptr, their f gives
+// col(M^r) and their o gives row(M^r) (fiber_ptr, empty rows kept).
+//
+// The sort is a least-significant-digit radix sort with 8-bit digits written
+// for this library: per-tile digit histograms, a device-wide scan, and a stable
+// scatter that ranks equal digits inside a warp with __match_any_sync.  Keys
+// of up to 64 bits sort in one run; wider (o, f, in) keys take two stable runs
+// (first by `in`, then by (o, f)).
+#include <algorithm>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace dfacto {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 16;
+constexpr int64_t kSortTile = (int64_t)kSortThreads * kSortRounds;
+constexpr int kDigits = 256;
+
+int nbits_for(int64_t dim) {  // bits needed for values 0 .. dim-1
+  int b = 0;
+  while (b < 63 && (int64_t(1) << b) < dim) ++b;
+  return b;
+}
+
+__global__ void check_range(const int32_t* __restrict__ idx, int64_t nnz, int32_t d0, int32_t d1,
+                            int32_t d2, int32_t* __restrict__ flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += stride) {
+    const int32_t i = idx[t], j = idx[nnz + t], k = idx[2 * nnz + t];
+    bad |= (i < 0) | (i >= d0) | (j < 0) | (j >= d1) | (k < 0) | (k >= d2);
+  }
+  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+// ||X||^2: squares and partial sums in FP64, one partial per block.
+__global__ void sumsq_partials(const float* __restrict__ val, int64_t n, double* __restrict__ part) {
+  __shared__ double s[32];
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    const double x = val[t];
+    acc += x * x;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void sum_partials(const double* __restrict__ part, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += part[i];  // fixed order: deterministic
+    *out = t;
+  }
+}
+
+// Composite key for keys that fit in 64 bits: (o << (bf + bi)) | (f << bi) | in.
+__global__ void make_keys64(const int32_t* __restrict__ idx, int64_t nnz, int ao, int af, int ai,
+                            int bf, int bi, uint64_t* __restrict__ key, uint32_t* __restrict__ perm) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += stride) {
+    const uint64_t o = (uint32_t)idx[ao * nnz + t], f = (uint32_t)idx[af * nnz + t],
+                   in = (uint32_t)idx[ai * nnz + t];
+    key[t] = ((bf + bi >= 64) ? 0ull : (o << (bf + bi))) | (f << bi) | in;
+    perm[t] = (uint32_t)t;
+  }
+}
+
+// First run of a wide key: sort by `in` alone.
+__global__ void make_keys_in(const int32_t* __restrict__ idx, int64_t nnz, int ai,
+                             uint64_t* __restrict__ key, uint32_t* __restrict__ perm) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += stride) {
+    key[t] = (uint32_t)idx[ai * nnz + t];
+    perm[t] = (uint32_t)t;
+  }
+}
+
+// Second run of a wide key: (o << bf) | f of the element now at position p.
+__global__ void make_keys_of(const int32_t* __restrict__ idx, int64_t nnz, int ao, int af, int bf,
+                             const uint32_t* __restrict__ perm, uint64_t* __restrict__ key) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+    const int64_t t = perm[p];
+    key[p] = ((uint64_t)(uint32_t)idx[ao * nnz + t] << bf) | (uint32_t)idx[af * nnz + t];
+  }
+}
+
+// Per-tile digit counts, written digit-major: cnt[d * ntiles + tile].
+__global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __restrict__ key,
+                                                          int64_t n, int shift,
+                                                          int32_t* __restrict__ cnt, int64_t ntiles) {
+  __shared__ int32_t s_cnt[kDigits];
+  s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  const int lane = threadIdx.x & 31;
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    const bool ok = i < n;
+    const int d = ok ? (int)((key[i] >> shift) & 0xff) : kDigits;
+    const unsigned peers = __match_any_sync(kFull, d);
+    if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[d], __popc(peers));
+  }
+  __syncthreads();
+  cnt[(int64_t)threadIdx.x * ntiles + blockIdx.x] = s_cnt[threadIdx.x];
+}
+
+// Stable scatter of one tile: element order inside a tile is round, then warp,
+// then lane, and equal digits keep that order.
+__global__ void __launch_bounds__(kSortThreads) radix_scatter(
+    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, int64_t n, int shift, const int32_t* __restrict__ ofs,
+    int64_t ntiles) {
+  constexpr int kWarps = kSortThreads / 32;
+  __shared__ int32_t s_cnt[kWarps][kDigits];
+  __shared__ int32_t s_run[kDigits];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  s_run[threadIdx.x] = ofs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    const bool ok = i < n;
+    const uint64_t k = ok ? kin[i] : 0;
+    const uint32_t v = ok ? vin[i] : 0;
+    const int d = ok ? (int)((k >> shift) & 0xff) : kDigits;
+    const unsigned peers = __match_any_sync(kFull, d);
+    const int rank = __popc(peers & lt);
+#pragma unroll
+    for (int q = 0; q < kDigits / 32; ++q) s_cnt[warp][lane + 32 * q] = 0;
+    __syncwarp();
+    if (ok && rank == 0) s_cnt[warp][d] = __popc(peers);
+    __syncthreads();
+    {
+      const int dd = threadIdx.x;  // one digit per thread
+      int32_t run = s_run[dd];
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) {
+        const int32_t c = s_cnt[w][dd];
+        s_cnt[w][dd] = run;
+        run += c;
+      }
+      s_run[dd] = run;
+    }
+    __syncthreads();
+    if (ok) {
+      const int64_t pos = (int64_t)s_cnt[warp][d] + rank;
+      kout[pos] = k;
+      vout[pos] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// After the sort: fiber-start flags, duplicate detection, nz_idx and nz_val.
+// narrow: key = (o,f,in) packed with `in` in the low bi bits.
+// wide:   key = (o,f) packed; `in` comes from the COO through perm.
+__global__ void segment_flags(const uint64_t* __restrict__ key, const uint32_t* __restrict__ perm,
+                              int64_t n, int bi, bool wide, const int32_t* __restrict__ idx, int ai,
+                              const float* __restrict__ val, int32_t* __restrict__ head,
+                              int32_t* __restrict__ nz_idx, float* __restrict__ nz_val,
+                              int32_t* __restrict__ dup_flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool dup = false;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    const uint64_t k = key[p];
+    const int64_t t = perm[p];
+    int32_t in;
+    uint64_t fkey;
+    if (wide) {
+      in = idx[ai * n + t];
+      fkey = k;
+    } else {
+      in = (int32_t)(k & ((bi >= 64) ? ~0ull : ((1ull << bi) - 1ull)));
+      fkey = (bi >= 64) ? 0 : (k >> bi);
+    }
+    int32_t h = 1;
+    if (p > 0) {
+      const uint64_t kp = key[p - 1];
+      if (wide) {
+        if (kp == k) {
+          h = 0;
+          dup |= (idx[ai * n + perm[p - 1]] == in);
+        }
+      } else {
+        const uint64_t fp = (bi >= 64) ? 0 : (kp >> bi);
+        h = (fp != fkey);
+        dup |= (kp == k);
+      }
+    }
+    head[p] = h;
+    nz_idx[p] = in;
+    nz_val[p] = val[t];
+  }
+  if (__any_sync(kFull, dup) && (threadIdx.x & 31) == 0) atomicOr(dup_flag, 1);
+}
+
+__global__ void scatter_fibers(const uint64_t* __restrict__ key, const uint32_t* __restrict__ perm,
+                               int64_t n, int bf, int bi, bool wide, const int32_t* __restrict__ head,
+                               const int32_t* __restrict__ fid, int64_t* __restrict__ nz_ptr,
+                               int32_t* __restrict__ fiber_idx, int32_t* __restrict__ fiber_row,
+                               int64_t nfib) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    if (!head[p]) continue;
+    const uint64_t k = key[p];
+    const uint64_t of = wide ? k : ((bi >= 64) ? 0 : (k >> bi));
+    const uint64_t fmask = (bf >= 64) ? ~0ull : ((1ull << bf) - 1ull);
+    const int32_t q = fid[p];
+    nz_ptr[q] = p;
+    fiber_idx[q] = (int32_t)(of & fmask);
+    fiber_row[q] = (int32_t)((bf >= 64) ? 0 : (of >> bf));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) nz_ptr[nfib] = n;
+}
+
+// fiber_ptr[r] = number of fibers whose row is < r (lower bound in fiber_row).
+__global__ void row_pointers(const int32_t* __restrict__ fiber_row, int64_t nfib, int64_t dim_o,
+                             int64_t* __restrict__ fiber_ptr) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= dim_o; r += stride) {
+    int64_t lo = 0, hi = nfib;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (fiber_row[mid] < r) lo = mid + 1; else hi = mid;
+    }
+    fiber_ptr[r] = lo;
+  }
+}
+
+// seg_fib[s] = the fiber holding nonzero s*seg: the last q with nz_ptr[q] <= s*seg.
+__global__ void segment_starts(const int64_t* __restrict__ nz_ptr, int64_t nfib, int64_t nseg,
+                               int64_t seg, int32_t* __restrict__ seg_fib) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += stride) {
+    const int64_t p = s * seg;
+    int64_t lo = 0, hi = nfib;  // find first q with nz_ptr[q] > p, in [1, nfib]
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (nz_ptr[mid] <= p) lo = mid + 1; else hi = mid;
+    }
+    seg_fib[s] = (int32_t)(lo - 1);
+  }
+}
+
+unsigned grid_for(int64_t n, int threads = 256, int64_t cap = 152 * 32) {
+  int64_t b = (n + threads - 1) / threads;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, cap));
+}
+
+// Stable LSD radix sort of (key, val) pairs by bits [0, nbits).  The result is
+// left in (k0, v0) or (k1, v1); *in_alt tells which.
+cudaError_t radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
+                       int nbits, cudaStream_t s, bool* in_alt) {
+  *in_alt = false;
+  if (n <= 1 || nbits <= 0) return cudaSuccess;
+  const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+  int32_t* cnt = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&cnt),
+                                  sizeof(int32_t) * kDigits * ntiles, s);
+  if (e != cudaSuccess) return e;
+  const int passes = (nbits + 7) / 8;
+  uint64_t *ki = k0, *ko = k1;
+  uint32_t *vi = v0, *vo = v1;
+  for (int pass = 0; pass < passes && e == cudaSuccess; ++pass) {
+    const int shift = 8 * pass;
+    radix_hist<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n, shift, cnt, ntiles);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = exclusive_scan_i32(cnt, cnt, kDigits * ntiles, s);
+    if (e == cudaSuccess) {
+      radix_scatter<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, cnt, ntiles);
+      e = cudaGetLastError();
+    }
+    std::swap(ki, ko);
+    std::swap(vi, vo);
+    *in_alt = !*in_alt;
+  }
+  cudaError_t e2 = cudaFreeAsync(cnt, s);
+  return e != cudaSuccess ? e : e2;
+}
+
+}  // namespace
+
+dfacto_status ensure_segments(dfacto_t* h, int mode) {
+  ModeCSR& M = h->m[mode];
+  const int seg = M.cfg.seg;
+  if (M.seg_fib && M.seg_fib_for == seg) return DFACTO_OK;
+  if (M.seg_fib) {
+    dfree(h, M.seg_fib, sizeof(int32_t) * (size_t)std::max<int64_t>(M.nseg, 1));
+    M.seg_fib = nullptr;
+  }
+  M.nseg = (h->nnz + seg - 1) / seg;
+  dfacto_status st = dalloc(h, reinterpret_cast<void**>(&M.seg_fib),
+                            sizeof(int32_t) * (size_t)std::max<int64_t>(M.nseg, 1));
+  if (st != DFACTO_OK) return st;
+  if (M.nseg > 0) {
+    segment_starts<<<grid_for(M.nseg), 256, 0, h->stream>>>(M.nz_ptr, M.nfib, M.nseg, seg, M.seg_fib);
+    DF_CUDA(h, cudaGetLastError());
+  }
+  M.seg_fib_for = seg;
+  return DFACTO_OK;
+}
+
+dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->nnz;
+  DF_CUDA(h, cudaMemsetAsync(h->flags, 0, sizeof(int32_t) * kNumFlags, s));
+  if (n > 0) {
+    check_range<<<grid_for(n), 256, 0, s>>>(d_idx, n, h->dims[0], h->dims[1], h->dims[2],
+                                            h->flags + kFlagRange);
+    DF_CUDA(h, cudaGetLastError());
+    DF_CUDA(h, cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int32_t) * kNumFlags,
+                               cudaMemcpyDeviceToHost, s));
+    DF_CUDA(h, cudaStreamSynchronize(s));
+    if (h->host_flags[kFlagRange]) return fail(h, DFACTO_ERANGE, "a coordinate lies outside dims");
+  }
+  // ||X||^2 once (FP64).
+  {
+    const unsigned nb = grid_for(n, 256, 1024);
+    sumsq_partials<<<nb, 256, 0, s>>>(d_val, n, h->partials);
+    sum_partials<<<1, 32, 0, s>>>(h->partials, (int)nb, h->scal + kNormX2);
+    DF_CUDA(h, cudaGetLastError());
+  }
+
+  uint64_t *k0 = nullptr, *k1 = nullptr;
+  uint32_t *v0 = nullptr, *v1 = nullptr;
+  int32_t *head = nullptr, *fid = nullptr;
+  const size_t nn = (size_t)std::max<int64_t>(n, 1);
+  cudaError_t e = cudaSuccess;
+  auto cleanup = [&]() {
+    if (k0) cudaFreeAsync(k0, s);
+    if (k1) cudaFreeAsync(k1, s);
+    if (v0) cudaFreeAsync(v0, s);
+    if (v1) cudaFreeAsync(v1, s);
+    if (head) cudaFreeAsync(head, s);
+    if (fid) cudaFreeAsync(fid, s);
+  };
+  if (n > 0) {
+    e = cudaMallocAsync(reinterpret_cast<void**>(&k0), sizeof(uint64_t) * nn, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&k1), sizeof(uint64_t) * nn, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&v0), sizeof(uint32_t) * nn, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&v1), sizeof(uint32_t) * nn, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&head), sizeof(int32_t) * nn, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&fid), sizeof(int32_t) * nn, s);
+    if (e != cudaSuccess) {
+      cleanup();
+      cudaGetLastError();
+      return fail(h, e == cudaErrorMemoryAllocation ? DFACTO_ENOMEM : DFACTO_ECUDA,
+                  std::string("build scratch allocation: ") + cudaGetErrorString(e));
+    }
+  }
+
+  for (int mode = 0; mode < 3; ++mode) {
+    ModeCSR& M = h->m[mode];
+    M.o = mode;
+    M.in = (mode + 1) % 3;
+    M.f = (mode + 2) % 3;
+    M.dim_o = h->dims[M.o];
+    const int bo = nbits_for(h->dims[M.o]), bf = nbits_for(h->dims[M.f]),
+              bi = nbits_for(h->dims[M.in]);
+    const bool wide = bo + bf + bi > 64;
+    dfacto_status st = DFACTO_OK;
+    st = dalloc(h, reinterpret_cast<void**>(&M.fiber_ptr), sizeof(int64_t) * (size_t)(M.dim_o + 1));
+    if (st == DFACTO_OK) st = dalloc(h, reinterpret_cast<void**>(&M.nz_idx), sizeof(int32_t) * nn);
+    if (st == DFACTO_OK) st = dalloc(h, reinterpret_cast<void**>(&M.nz_val), sizeof(float) * nn);
+    if (st != DFACTO_OK) {
+      cleanup();
+      return st;
+    }
+    if (n == 0) {
+      M.nfib = 0;
+      st = dalloc(h, reinterpret_cast<void**>(&M.nz_ptr), sizeof(int64_t));
+      if (st == DFACTO_OK) st = dalloc(h, reinterpret_cast<void**>(&M.fiber_idx), sizeof(int32_t));
+      if (st == DFACTO_OK) st = dalloc(h, reinterpret_cast<void**>(&M.fiber_row), sizeof(int32_t));
+      if (st != DFACTO_OK) return st;
+      DF_CUDA(h, cudaMemsetAsync(M.nz_ptr, 0, sizeof(int64_t), s));
+      DF_CUDA(h, cudaMemsetAsync(M.fiber_ptr, 0, sizeof(int64_t) * (size_t)(M.dim_o + 1), s));
+      continue;
+    }
+    bool alt = false, alt2 = false;
+    if (!wide) {
+      make_keys64<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, M.in, bf, bi, k0, v0);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = radix_sort(k0, v0, k1, v1, n, bo + bf + bi, s, &alt);
+    } else {
+      make_keys_in<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.in, k0, v0);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = radix_sort(k0, v0, k1, v1, n, bi, s, &alt);
+      uint64_t* kk = alt ? k1 : k0;
+      uint32_t* vv = alt ? v1 : v0;
+      uint64_t* ko = alt ? k0 : k1;
+      uint32_t* vo = alt ? v0 : v1;
+      if (e == cudaSuccess) {
+        make_keys_of<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, bf, vv, kk);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = radix_sort(kk, vv, ko, vo, n, bo + bf, s, &alt2);
+      alt = alt ^ alt2;
+    }
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_fail(h, e, "radix sort");
+    }
+    const uint64_t* key = alt ? k1 : k0;
+    const uint32_t* perm = alt ? v1 : v0;
+    segment_flags<<<grid_for(n), 256, 0, s>>>(key, perm, n, bi, wide, d_idx, M.in, d_val, head,
+                                             M.nz_idx, M.nz_val, h->flags + kFlagDup);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = exclusive_scan_i32(head, fid, n, s);
+    int32_t last[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&last[0], fid + n - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&last[1], head + n - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_fail(h, e, "fiber segmentation");
+    }
+    M.nfib = (int64_t)last[0] + last[1];
+    st = dalloc(h, reinterpret_cast<void**>(&M.nz_ptr), sizeof(int64_t) * (size_t)(M.nfib + 1));
+    if (st == DFACTO_OK)
+      st = dalloc(h, reinterpret_cast<void**>(&M.fiber_idx), sizeof(int32_t) * (size_t)M.nfib);
+    if (st == DFACTO_OK)
+      st = dalloc(h, reinterpret_cast<void**>(&M.fiber_row), sizeof(int32_t) * (size_t)M.nfib);
+    if (st != DFACTO_OK) {
+      cleanup();
+      return st;
+    }
+    scatter_fibers<<<grid_for(n), 256, 0, s>>>(key, perm, n, bf, bi, wide, head, fid, M.nz_ptr,
+                                              M.fiber_idx, M.fiber_row, M.nfib);
+    row_pointers<<<grid_for(M.dim_o + 1), 256, 0, s>>>(M.fiber_row, M.nfib, M.dim_o, M.fiber_ptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_fail(h, e, "fiber arrays");
+    }
+  }
+  cleanup();
+  DF_CUDA(h, cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int32_t) * kNumFlags,
+                             cudaMemcpyDeviceToHost, s));
+  DF_CUDA(h, cudaStreamSynchronize(s));
+  if (h->host_flags[kFlagDup]) return fail(h, DFACTO_EDUP, "two nonzeros share a coordinate");
+  return DFACTO_OK;
+}
+
+}  // namespace dfacto

@@ -1,0 +1,218 @@
+// dual.cu -- the four trilinear terms the GD line search needs beyond the
+// MTTKRP outputs:
+//   T110 = <X, [[GA, GB, C ]]>,  T101 = <X, [[GA, B, GC]]>,
+//   T011 = <X, [[A,  GB, GC]]>,  T111 = <X, [[GA, GB, GC]]>,
+// all in one walk over the mode-1 CSR copy (rows i, fibers (i,k), entries j),
+// organised like Algorithm 1 with two inputs per SpMV: per fiber
+// vB = sum x B[j,:] and vG = sum x GB[j,:]; per row u1 = sum C[k,:] (*) vG,
+// u2 = sum GC[k,:] (*) vB, u3 = sum GC[k,:] (*) vG; then T110 += GA[i,:].u1,
+// T101 += GA[i,:].u2, T011 += A[i,:].u3, T111 += GA[i,:].u3.  Only scalars
+// leave the walk, so rows split between segments need no carries.  Segment sums
+// are FP32 (at most one segment of nonzeros), everything above is FP64.
+#include <algorithm>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace dfacto {
+namespace {
+
+struct DualParams {
+  const int32_t* fiber_idx;
+  const int32_t* fiber_row;
+  const int64_t* nz_ptr;
+  const int32_t* nz_idx;
+  const float* nz_val;
+  const int32_t* seg_fib;
+  const void* A;
+  const void* B;
+  const void* C;
+  const float* GA;
+  const float* GB;
+  const float* GC;
+  double* part;  // [ncta][4]
+  int64_t nnz;
+  int64_t nfib;
+  int R;
+  int seg;
+};
+
+template <typename T, int VEC, int G>
+__global__ void __launch_bounds__(kWalkWarps * 32) dual_walk(const DualParams a) {
+  constexpr int NG = 32 / G;
+  constexpr int SEGS = kWalkWarps * NG;
+  __shared__ double s_t[kWalkWarps][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / G, c = lane % G;
+  const int gbase = g * G;
+  const int col0 = c * VEC;
+  const bool colok = col0 < a.R;
+  const int sl = warp * NG + g;
+  const int64_t p0 = ((int64_t)blockIdx.x * SEGS + sl) * a.seg;
+  const int64_t p1 = min(p0 + a.seg, a.nnz);
+  const bool active = p0 < a.nnz;
+  const int R = a.R;
+  const T* A = static_cast<const T*>(a.A);
+  const T* B = static_cast<const T*>(a.B);
+  const T* C = static_cast<const T*>(a.C);
+
+  float vB[VEC], vG[VEC], cf[VEC], gcf[VEC], u1[VEC], u2[VEC], u3[VEC];
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) vB[q] = vG[q] = cf[q] = gcf[q] = u1[q] = u2[q] = u3[q] = 0.f;
+  float t[4] = {0.f, 0.f, 0.f, 0.f};
+
+  int64_t fib = 0, fend = 0;
+  int row_cur = -1;
+  auto load_fiber = [&](int64_t q) {
+    fend = min(a.nz_ptr[q + 1], p1);
+    row_cur = a.fiber_row[q];
+    const int k = a.fiber_idx[q];
+    if (colok) {
+      VecIO<T, VEC>::load(C + (int64_t)k * R + col0, cf);
+      VecIO<float, VEC>::load(a.GC + (int64_t)k * R + col0, gcf);
+    }
+  };
+  auto emit_row = [&]() {
+    if (!colok) return;
+    float ar[VEC], gar[VEC];
+    VecIO<T, VEC>::load(A + (int64_t)row_cur * R + col0, ar);
+    VecIO<float, VEC>::load(a.GA + (int64_t)row_cur * R + col0, gar);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+      t[0] = fmaf(gar[q], u1[q], t[0]);
+      t[1] = fmaf(gar[q], u2[q], t[1]);
+      t[2] = fmaf(ar[q], u3[q], t[2]);
+      t[3] = fmaf(gar[q], u3[q], t[3]);
+      u1[q] = u2[q] = u3[q] = 0.f;
+    }
+  };
+  if (active) {
+    fib = a.seg_fib[(int64_t)blockIdx.x * SEGS + sl];
+    load_fiber(fib);
+  }
+  for (int64_t base = p0; base < p0 + a.seg; base += G) {
+    const int64_t pl = base + c;
+    const bool okl = pl < p1;
+    const int my_in = okl ? __ldg(a.nz_idx + pl) : 0;
+    const float my_x = okl ? __ldg(a.nz_val + pl) : 0.f;
+#pragma unroll 1
+    for (int u = 0; u < G; ++u) {
+      const int j = __shfl_sync(kFull, my_in, gbase + u);
+      const float x = __shfl_sync(kFull, my_x, gbase + u);
+      const int64_t p = base + u;
+      if (p < p1) {
+        if (colok) {
+          float b[VEC], gb[VEC];
+          VecIO<T, VEC>::load(B + (int64_t)j * R + col0, b);
+          VecIO<float, VEC>::load(a.GB + (int64_t)j * R + col0, gb);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) {
+            vB[q] = fmaf(x, b[q], vB[q]);
+            vG[q] = fmaf(x, gb[q], vG[q]);
+          }
+        }
+        if (p + 1 == fend) {
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) {
+            u1[q] = fmaf(cf[q], vG[q], u1[q]);
+            u2[q] = fmaf(gcf[q], vB[q], u2[q]);
+            u3[q] = fmaf(gcf[q], vG[q], u3[q]);
+            vB[q] = vG[q] = 0.f;
+          }
+          if (p + 1 < p1) {
+            const int old_row = row_cur;
+            ++fib;
+            const int64_t save_fib = fib;
+            // peek the next fiber's row before loading it
+            const int next_row = a.fiber_row[save_fib];
+            if (next_row != old_row) emit_row();
+            load_fiber(save_fib);
+          }
+        }
+      }
+    }
+  }
+  if (active) emit_row();
+  double td[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    td[k] = warp_sum((double)t[k]);
+    if (lane == 0) s_t[warp][k] = td[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double s = 0.0;
+    for (int w = 0; w < kWalkWarps; ++w) s += s_t[w][threadIdx.x];
+    a.part[(size_t)blockIdx.x * 4 + threadIdx.x] = s;
+  }
+}
+
+__global__ void dual_reduce(const double* __restrict__ part, int64_t ncta, double* __restrict__ scal) {
+  if (threadIdx.x < 4) {
+    double s = 0.0;
+    for (int64_t b = 0; b < ncta; ++b) s += part[b * 4 + threadIdx.x];
+    scal[kT110 + threadIdx.x] = s;
+  }
+}
+
+template <typename T, int VEC, int G>
+cudaError_t go(const DualParams& a, int64_t ncta, cudaStream_t s) {
+  dual_walk<T, VEC, G><<<(unsigned)ncta, kWalkWarps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch(int vec, int G, const DualParams& a, int64_t ncta, cudaStream_t s) {
+#define DF_CASE(V, GG) \
+  if (vec == V && G == GG) return go<T, V, GG>(a, ncta, s);
+  DF_CASE(1, 1) DF_CASE(1, 2) DF_CASE(1, 4) DF_CASE(1, 8) DF_CASE(1, 16) DF_CASE(1, 32)
+  DF_CASE(2, 1) DF_CASE(2, 2) DF_CASE(2, 4) DF_CASE(2, 8) DF_CASE(2, 16) DF_CASE(2, 32)
+  DF_CASE(4, 1) DF_CASE(4, 2) DF_CASE(4, 4) DF_CASE(4, 8) DF_CASE(4, 16) DF_CASE(4, 32)
+  DF_CASE(8, 1) DF_CASE(8, 2) DF_CASE(8, 4) DF_CASE(8, 8) DF_CASE(8, 16)
+#undef DF_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+dfacto_status dual_pass(dfacto_t* h) {
+  ModeCSR& M = h->m[0];
+  dfacto_status st = ensure_segments(h, 0);
+  if (st != DFACTO_OK) return st;
+  const WalkCfg cfg = M.cfg;
+  const int segs = kWalkWarps * (32 / cfg.G);
+  const int64_t P = (int64_t)segs * cfg.seg;
+  const int64_t ncta = (h->nnz + P - 1) / P;
+  if ((st = grow_partials(h, ncta * 4)) != DFACTO_OK) return st;
+  if (ncta == 0) {
+    DF_CUDA(h, cudaMemsetAsync(h->scal + kT110, 0, 4 * sizeof(double), h->stream));
+    return DFACTO_OK;
+  }
+  DualParams a;
+  a.fiber_idx = M.fiber_idx;
+  a.fiber_row = M.fiber_row;
+  a.nz_ptr = M.nz_ptr;
+  a.nz_idx = M.nz_idx;
+  a.nz_val = M.nz_val;
+  a.seg_fib = M.seg_fib;
+  a.A = h->F[0];
+  a.B = h->F[1];
+  a.C = h->F[2];
+  a.GA = h->grad[0];
+  a.GB = h->grad[1];
+  a.GC = h->grad[2];
+  a.part = h->partials;
+  a.nnz = h->nnz;
+  a.nfib = M.nfib;
+  a.R = h->R;
+  a.seg = cfg.seg;
+  cudaError_t e = (h->dtype == DFACTO_BF16)
+                      ? launch<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, h->stream)
+                      : launch<float>(cfg.vec, cfg.G, a, ncta, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "dual_walk launch");
+  dual_reduce<<<1, 32, 0, h->stream>>>(h->partials, ncta, h->scal);
+  DF_CUDA(h, cudaGetLastError());
+  return DFACTO_OK;
+}
+
+}  // namespace dfacto

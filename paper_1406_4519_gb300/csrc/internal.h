@@ -1,0 +1,144 @@
+// internal.h -- private state of a libdfacto handle and the host-side entry
+// points of each kernel family.  Not part of the public ABI (include/dfacto.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/dfacto.h"
+
+namespace dfacto {
+
+// Lane-group configuration of the MTTKRP walk: each group of G lanes owns one
+// segment of the nonzero stream and each lane owns VEC consecutive columns.
+struct WalkCfg {
+  int vec = 0;    // columns per lane (1, 2, 4, 8)
+  int G = 0;      // lanes per group (power of two, G * vec >= R)
+  int seg = 0;    // nonzeros per segment (multiple of 32)
+};
+
+constexpr int kWalkWarps = 8;  // warps per MTTKRP CTA
+
+// Flattened CSR copy of one mode (Sec. 3): the nonzero rows of
+// (X^{n+1})^T ("fibers") and the fixed pattern of M^r.
+struct ModeCSR {
+  int o = 0, in = 0, f = 0;    // axes
+  int64_t dim_o = 0;
+  int64_t nfib = 0;
+  int64_t* fiber_ptr = nullptr;  // [dim_o + 1]  row(M^r)
+  int32_t* fiber_idx = nullptr;  // [nfib]       col(M^r) = f
+  int32_t* fiber_row = nullptr;  // [nfib]       o of each fiber (COO form of row(M^r))
+  int64_t* nz_ptr = nullptr;     // [nfib + 1]
+  int32_t* nz_idx = nullptr;     // [nnz]        index `in`
+  float* nz_val = nullptr;       // [nnz]
+  WalkCfg cfg;
+  int64_t nseg = 0;              // segments of cfg.seg nonzeros
+  int32_t* seg_fib = nullptr;    // [nseg] fiber holding the first nonzero of each segment
+  int32_t seg_fib_for = 0;       // segment length seg_fib was computed for
+};
+
+// Scalar slots in device memory (double).
+enum Scalar : int {
+  kNormX2 = 0,   // ||X||^2
+  kFit,          // last fit
+  kInner,        // <X, Xhat>
+  kLoss,         // GD objective at the current point
+  kAlpha,        // last accepted GD step (alpha_prev)
+  kG2,           // ||grad||^2
+  kModelNorm2,   // ||Xhat||^2
+  kT000, kT100, kT010, kT001, kT110, kT101, kT011, kT111,  // GD trilinear terms
+  kStep,         // step applied by the last GD update (0 after a failed search)
+  kNumScalars
+};
+
+// Integer status flags in device memory.
+enum Flag : int {
+  kFlagRange = 0,     // coordinate out of range
+  kFlagDup,           // duplicate coordinate
+  kFlagSingular,      // a pseudo-inverse was used
+  kFlagLsFail,        // line search failed
+  kFlagInternal,      // internal check failed
+  kNumFlags
+};
+
+}  // namespace dfacto
+
+struct dfacto_handle {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int32_t dims[3] = {0, 0, 0};
+  int64_t nnz = 0;
+  int R = 1;
+  int dtype = DFACTO_F32;  // factor storage
+  double lambda_reg = 0.0;
+  dfacto_options opt{};
+  dfacto::ModeCSR m[3];
+  void* F[3] = {nullptr, nullptr, nullptr};   // factors, storage dtype
+  float* N = nullptr;                         // [max dim x R] MTTKRP output scratch
+  float* grad[3] = {nullptr, nullptr, nullptr};  // GD gradients (lazy)
+  double* lambda = nullptr;                   // [R]
+  float* inv_lambda = nullptr;                // [R] 1/lambda (1 where lambda = 0)
+  double* ipart = nullptr;                    // [blocks x R] partials of <X, Xhat>
+  int ipart_blocks = 0;
+  double* gram[3] = {nullptr, nullptr, nullptr};  // [R x R] Grams of the stored factors
+  bool gram_valid[3] = {false, false, false};
+  double* gd_mats = nullptr;                  // [3 x 3 x R x R] P0/P1/P2 per factor
+  double* W = nullptr;                        // [R x R] Gamma^{-1} (FP64)
+  double* rr_work = nullptr;                  // [2 R^2 + R] workspace of the R x R solve
+  float* W32 = nullptr;                       // [R x R] Gamma^{-1} (FP32)
+  double* scal = nullptr;                     // [kNumScalars]
+  int32_t* flags = nullptr;                   // [kNumFlags]
+  double* partials = nullptr;                 // reduction partials
+  int64_t partials_cap = 0;                   // doubles
+  float* carry = nullptr;                     // MTTKRP CTA carries [ncta x 2 x R]
+  int32_t* carry_row = nullptr;               // [ncta x 4] head row, tail row, slot info
+  int64_t carry_cap = 0;                      // CTAs
+  double* host_scal = nullptr;                // pinned mirror of scal
+  int32_t* host_flags = nullptr;              // pinned mirror of flags
+  int64_t bytes = 0;
+  std::string err;
+};
+
+namespace dfacto {
+
+// ---- errors ---------------------------------------------------------------
+dfacto_status fail(dfacto_t* h, dfacto_status s, const std::string& what);
+dfacto_status cuda_fail(dfacto_t* h, cudaError_t e, const char* what);
+#define DF_CUDA(h, call)                                              \
+  do {                                                                \
+    cudaError_t e_ = (call);                                          \
+    if (e_ != cudaSuccess) return ::dfacto::cuda_fail((h), e_, #call); \
+  } while (0)
+
+// ---- memory ---------------------------------------------------------------
+dfacto_status dalloc(dfacto_t* h, void** p, size_t bytes);
+void dfree(dfacto_t* h, void* p, size_t bytes);
+bool is_device_ptr(const void* p);
+dfacto_status grow_partials(dfacto_t* h, int64_t doubles);
+
+// ---- scan (scan.cu) -------------------------------------------------------
+// Exclusive prefix sum of n int32 values (n < 2^31), out may alias in.
+// Temporary storage is taken with cudaMallocAsync on `s`.
+cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s);
+
+// ---- build (build.cu) -----------------------------------------------------
+dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val);
+dfacto_status ensure_segments(dfacto_t* h, int mode);
+
+// ---- MTTKRP (mttkrp*.cu) --------------------------------------------------
+WalkCfg choose_walk(int R, int dtype, int64_t nnz, int64_t nfib, int seg_opt, int vec_opt);
+dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out);
+
+// ---- dense R x R and row-wise kernels (dense.cu) --------------------------
+dfacto_status gram_of_factor(dfacto_t* h, int m);
+dfacto_status als_mode(dfacto_t* h, int mode);
+dfacto_status als_fit(dfacto_t* h);
+dfacto_status fit_direct(dfacto_t* h);
+dfacto_status gd_step(dfacto_t* h);
+dfacto_status convert_factor_in(dfacto_t* h, int m, const void* src, int src_dtype);
+dfacto_status convert_factor_out(dfacto_t* h, int m, void* dst, int dst_dtype);
+dfacto_status norm_x2(dfacto_t* h);
+
+}  // namespace dfacto

@@ -1,0 +1,153 @@
+// mttkrp.cu -- host side of the MTTKRP: configuration, launch, and the carry
+// fix-up kernel that finishes rows spanning several CTAs and zero-fills rows
+// with no nonzeros.
+#include <algorithm>
+
+#include "mttkrp.cuh"
+
+namespace dfacto {
+namespace {
+
+constexpr int kFixThreads = 256;
+
+// One block per CTA c (grid-stride): if c's last partial run belongs to a row r
+// that starts inside c, add up r's partials from CTAs c .. c_last in CTA order
+// (eight warps take interleaved entries, then their sums are added in warp
+// order) and store N[r, :].  Then all blocks zero the rows without fibers.
+__global__ void __launch_bounds__(kFixThreads) mttkrp_fixup(
+    const int32_t* __restrict__ carry_row, const float* __restrict__ carry,
+    const int64_t* __restrict__ fiber_ptr, const int64_t* __restrict__ nz_ptr, float* __restrict__ out,
+    int R, int64_t P, int64_t ncta, int64_t dim_o, int32_t* __restrict__ bad) {
+  __shared__ float part[kFixThreads / 32][128];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t c = blockIdx.x; c < ncta; c += gridDim.x) {
+    const int k = carry_row[2 * c + 1] >= 0 ? 1 : 0;
+    const int r = carry_row[2 * c + k];
+    if (r < 0) continue;
+    const int64_t rb = nz_ptr[fiber_ptr[r]];
+    if (rb < c * P) continue;  // r started in an earlier CTA, which owns it
+    const int64_t re = nz_ptr[fiber_ptr[r + 1]];
+    const int64_t clast = (re - 1) / P;
+    const int64_t ne = clast - c + 1;
+    float s[kMaxColsPerLane];
+#pragma unroll
+    for (int q = 0; q < kMaxColsPerLane; ++q) s[q] = 0.f;
+    for (int64_t j = warp; j < ne; j += kFixThreads / 32) {
+      const int64_t entry = (j == 0) ? (2 * c + k) : (2 * (c + j));
+      if (j > 0 && lane == 0 && carry_row[entry] != r) atomicOr(bad, 1);
+#pragma unroll
+      for (int q = 0; q < kMaxColsPerLane; ++q) {
+        const int col = lane + 32 * q;
+        if (col < R) s[q] += carry[entry * R + col];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxColsPerLane; ++q) {
+      const int col = lane + 32 * q;
+      if (col < R) part[warp][col] = s[q];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int q = 0; q < kMaxColsPerLane; ++q) {
+        const int col = lane + 32 * q;
+        if (col < R) {
+          float t = 0.f;
+          for (int w = 0; w < kFixThreads / 32; ++w) t += part[w][col];
+          out[(int64_t)r * R + col] = t;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < dim_o; o += stride) {
+    if (fiber_ptr[o] == fiber_ptr[o + 1]) {
+      float* row = out + o * R;
+      for (int col = 0; col < R; ++col) row[col] = 0.f;
+    }
+  }
+}
+
+int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+WalkCfg choose_walk(int R, int dtype, int64_t nnz, int64_t nfib, int seg_opt, int vec_opt) {
+  (void)nnz;
+  (void)nfib;
+  WalkCfg c;
+  const int elem = dtype == DFACTO_BF16 ? 2 : 4;
+  int vec = vec_opt > 0 ? vec_opt : 16 / elem;
+  while (vec > 1 && (R % vec) != 0) vec >>= 1;
+  int G = next_pow2((R + vec - 1) / vec);
+  while (G > 32 && vec < 8 && (R % (vec * 2)) == 0) {
+    vec *= 2;
+    G = next_pow2((R + vec - 1) / vec);
+  }
+  c.vec = vec;
+  c.G = G;
+  int seg = seg_opt > 0 ? seg_opt : 256;
+  seg = std::max(32, (seg + 31) / 32 * 32);
+  c.seg = seg;
+  return c;
+}
+
+dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out) {
+  ModeCSR& M = h->m[mode];
+  const WalkCfg& cfg = M.cfg;
+  dfacto_status st = ensure_segments(h, mode);
+  if (st != DFACTO_OK) return st;
+  const int segs = kWalkWarps * (32 / cfg.G);
+  const int64_t P = (int64_t)segs * cfg.seg;
+  const int64_t ncta = (h->nnz + P - 1) / P;
+  if (ncta > h->carry_cap) {
+    if (h->carry) dfree(h, h->carry, sizeof(float) * 2 * (size_t)h->R * h->carry_cap);
+    if (h->carry_row) dfree(h, h->carry_row, sizeof(int32_t) * 2 * (size_t)h->carry_cap);
+    h->carry = nullptr;
+    h->carry_row = nullptr;
+    h->carry_cap = 0;
+    st = dalloc(h, reinterpret_cast<void**>(&h->carry), sizeof(float) * 2 * (size_t)h->R * ncta);
+    if (st == DFACTO_OK)
+      st = dalloc(h, reinterpret_cast<void**>(&h->carry_row), sizeof(int32_t) * 2 * (size_t)ncta);
+    if (st != DFACTO_OK) return st;
+    h->carry_cap = ncta;
+  }
+  MttkrpParams a;
+  a.fiber_ptr = M.fiber_ptr;
+  a.fiber_idx = M.fiber_idx;
+  a.fiber_row = M.fiber_row;
+  a.nz_ptr = M.nz_ptr;
+  a.nz_idx = M.nz_idx;
+  a.nz_val = M.nz_val;
+  a.seg_fib = M.seg_fib;
+  a.Fin = h->F[M.in];
+  a.Ff = h->F[M.f];
+  a.out = out;
+  a.carry = h->carry;
+  a.carry_row = h->carry_row;
+  a.nnz = h->nnz;
+  a.nfib = M.nfib;
+  a.R = h->R;
+  a.seg = cfg.seg;
+  if (ncta > 0) {
+    const size_t smem = sizeof(float) * (size_t)(2 * segs + 2 * kWalkWarps) * h->R;
+    cudaError_t e = (h->dtype == DFACTO_BF16)
+                        ? launch_walk<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, smem, h->stream)
+                        : launch_walk<float>(cfg.vec, cfg.G, a, ncta, smem, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mttkrp_walk launch");
+  }
+  const int64_t zero_blocks = (M.dim_o + kFixThreads - 1) / kFixThreads;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(std::max(ncta, zero_blocks), 152 * 16));
+  mttkrp_fixup<<<(unsigned)blocks, kFixThreads, 0, h->stream>>>(
+      h->carry_row, h->carry, M.fiber_ptr, M.nz_ptr, out, h->R, P, ncta, M.dim_o,
+      h->flags + kFlagInternal);
+  DF_CUDA(h, cudaGetLastError());
+  return DFACTO_OK;
+}
+
+}  // namespace dfacto

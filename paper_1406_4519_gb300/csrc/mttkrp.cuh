@@ -1,0 +1,283 @@
+// mttkrp.cuh -- the fused two-SpMV MTTKRP of DFacTo (Algorithm 1), batched
+// over all R columns.
+//
+// For mode n and every output row o:
+//   N[o, :] = sum over fibers q = (o, f) of  F_f[f, :] (*) v_q,
+//   v_q     = sum over nonzeros (in, x) of fiber q of  x * F_in[in, :],
+// where v_q is row q of value(M^r) for all r at once (first SpMV, (Xhat)^T b_r)
+// and the outer sum is the second SpMV, M^r c_r.  v_q never leaves registers.
+//
+// Work split (GB300): the nonzero stream is cut into segments of `seg`
+// nonzeros, independent of row and fiber boundaries, so heavy (power-law)
+// rows and fibers are spread over many lanes.  A group of G lanes walks one
+// segment; each lane owns VEC consecutive columns and gathers them with one
+// vector load per factor row.  The group's lanes fetch G upcoming (in, x)
+// pairs with one coalesced load and pass them around by shuffles.  Splitting
+// inside a fiber is exact because the second SpMV is linear in v.
+//
+// A row finished inside a segment is stored directly.  A segment's first and
+// last rows may continue into neighbouring segments: their partial sums go to
+// shared memory and are merged in segment order, first inside each warp, then
+// across the CTA's warps.  Rows that continue beyond the CTA's range are left
+// as per-CTA carries that mttkrp_fixup adds up in CTA order.  Every sum
+// therefore has a fixed order: results are bitwise reproducible.
+#pragma once
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace dfacto {
+
+struct MttkrpParams {
+  const int64_t* fiber_ptr;
+  const int32_t* fiber_idx;
+  const int32_t* fiber_row;
+  const int64_t* nz_ptr;
+  const int32_t* nz_idx;
+  const float* nz_val;
+  const int32_t* seg_fib;
+  const void* Fin;
+  const void* Ff;
+  float* out;
+  float* carry;       // [ncta][2][R]
+  int32_t* carry_row; // [ncta][2]
+  int64_t nnz;
+  int64_t nfib;
+  int R;
+  int seg;
+};
+
+constexpr int kMaxColsPerLane = 4;  // R <= 128 in the CTA merge (lane-strided columns)
+
+// Merge a sequence of (row, partial) entries into runs of equal rows, in order.
+// flush(row, vals, is_first, is_last) is called once per run; is_first/is_last
+// say whether the run contains the first/last valid entry.  Executed by one
+// full warp; lane handles columns lane, lane+32, ...
+template <typename Flush>
+__device__ __forceinline__ void merge_runs(const int32_t* rows, const float* vals, int count, int R,
+                                           int lane, Flush&& flush) {
+  int run_row = -1;
+  bool run_first = true;
+  float run[kMaxColsPerLane];
+#pragma unroll
+  for (int k = 0; k < kMaxColsPerLane; ++k) run[k] = 0.f;
+  for (int e = 0; e < count; ++e) {
+    const int row = rows[e];
+    if (row < 0) continue;
+    if (row != run_row) {
+      if (run_row >= 0) {
+        flush(run_row, run, run_first, false);
+        run_first = false;
+      }
+      run_row = row;
+#pragma unroll
+      for (int k = 0; k < kMaxColsPerLane; ++k) run[k] = 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxColsPerLane; ++k) {
+      const int col = lane + 32 * k;
+      if (col < R) run[k] += vals[(size_t)e * R + col];
+    }
+  }
+  if (run_row >= 0) flush(run_row, run, run_first, true);
+}
+
+template <typename T, int VEC, int G>
+__global__ void __launch_bounds__(kWalkWarps * 32) mttkrp_walk(const MttkrpParams a) {
+  constexpr int NG = 32 / G;
+  constexpr int SEGS = kWalkWarps * NG;
+  extern __shared__ float smem[];
+  float* s_val = smem;                          // [SEGS * 2][R]
+  float* w_val = smem + (size_t)SEGS * 2 * a.R; // [kWalkWarps * 2][R]
+  __shared__ int32_t s_row[SEGS * 2];
+  __shared__ int32_t w_row[kWalkWarps * 2];
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / G, c = lane % G;
+  const int gbase = g * G;
+  const int col0 = c * VEC;
+  const bool colok = col0 < a.R;
+  const int sl = warp * NG + g;  // segment index inside the CTA
+  const int64_t cta_p0 = (int64_t)blockIdx.x * SEGS * a.seg;
+  const int64_t cta_p1 = min(cta_p0 + (int64_t)SEGS * a.seg, a.nnz);
+  const int64_t p0 = cta_p0 + (int64_t)sl * a.seg;
+  const int64_t p1 = min(p0 + a.seg, a.nnz);
+  const bool active = p0 < a.nnz;
+  const T* __restrict__ Fin = static_cast<const T*>(a.Fin);
+  const T* __restrict__ Ff = static_cast<const T*>(a.Ff);
+  const int R = a.R;
+
+  float v[VEC], acc[VEC], ffc[VEC];
+#pragma unroll
+  for (int k = 0; k < VEC; ++k) { v[k] = 0.f; acc[k] = 0.f; ffc[k] = 0.f; }
+
+  int64_t fib = 0, fend = 0, fend_next = 0;
+  int row_cur = -1, row_next = -1, f_next = 0;
+  if (active) {
+    fib = a.seg_fib[(int64_t)blockIdx.x * SEGS + sl];
+    fend = min(a.nz_ptr[fib + 1], p1);
+    row_cur = a.fiber_row[fib];
+    if (colok) VecIO<T, VEC>::load(Ff + (int64_t)a.fiber_idx[fib] * R + col0, ffc);
+    if (fib + 1 < a.nfib) {
+      fend_next = a.nz_ptr[fib + 2];
+      f_next = a.fiber_idx[fib + 1];
+      row_next = a.fiber_row[fib + 1];
+    }
+  }
+
+  auto put_slot = [&](int k, int row, const float (&val)[VEC]) {
+    if (c == 0) s_row[sl * 2 + k] = row;
+    if (colok) {
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) s_val[(size_t)(sl * 2 + k) * R + col0 + q] = val[q];
+    }
+  };
+  bool head_open = true;
+
+  for (int64_t base = p0; base < p0 + a.seg; base += G) {
+    const int64_t pl = base + c;
+    const bool okl = pl < p1;
+    const int my_in = okl ? __ldg(a.nz_idx + pl) : 0;
+    const float my_x = okl ? __ldg(a.nz_val + pl) : 0.f;
+    // Row gathers are issued U at a time before any is used (memory-level
+    // parallelism), U * VEC <= 32 registers.
+    constexpr int U = (G < 32 / VEC) ? G : (32 / VEC);
+#pragma unroll
+    for (int u0 = 0; u0 < G; u0 += U) {
+      float fin[U][VEC];
+#pragma unroll
+      for (int uu = 0; uu < U; ++uu) {
+        const int in = __shfl_sync(kFull, my_in, gbase + u0 + uu);
+        if (colok && base + u0 + uu < p1) {
+          VecIO<T, VEC>::load(Fin + (int64_t)in * R + col0, fin[uu]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) fin[uu][q] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int uu = 0; uu < U; ++uu) {
+        const float x = __shfl_sync(kFull, my_x, gbase + u0 + uu);
+        const int64_t p = base + u0 + uu;
+        if (p < p1) {
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) v[q] = fmaf(x, fin[uu][q], v[q]);
+          if (p + 1 == fend) {  // the fiber (or its part in this segment) ends
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+              acc[q] = fmaf(v[q], ffc[q], acc[q]);
+              v[q] = 0.f;
+            }
+            if (p + 1 < p1) {  // next fiber starts inside this segment
+              ++fib;
+              fend = min(fend_next, p1);
+              if (row_next != row_cur) {
+                if (head_open) {
+                  put_slot(0, row_cur, acc);
+                  head_open = false;
+                } else if (colok) {
+                  VecIO<float, VEC>::store(a.out + (int64_t)row_cur * R + col0, acc);
+                }
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) acc[q] = 0.f;
+                row_cur = row_next;
+              }
+              if (colok) VecIO<T, VEC>::load(Ff + (int64_t)f_next * R + col0, ffc);
+              if (fib + 1 < a.nfib) {
+                fend_next = __ldg(a.nz_ptr + fib + 2);
+                f_next = __ldg(a.fiber_idx + fib + 1);
+                row_next = __ldg(a.fiber_row + fib + 1);
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+
+  // Segment slots: 0 = head row partial, 1 = tail row partial (-1 = none).
+  if (!active) {
+    if (c == 0) { s_row[sl * 2] = -1; s_row[sl * 2 + 1] = -1; }
+  } else if (head_open) {
+    put_slot(0, row_cur, acc);
+    if (c == 0) s_row[sl * 2 + 1] = -1;
+  } else {
+    put_slot(1, row_cur, acc);
+  }
+  __syncthreads();
+
+  // Level 1: each warp merges its NG segments.  Runs strictly inside the
+  // warp's range are complete rows.
+  {
+    if (lane == 0) { w_row[warp * 2] = -1; w_row[warp * 2 + 1] = -1; }
+    __syncwarp();
+    merge_runs(s_row + warp * NG * 2, s_val + (size_t)warp * NG * 2 * R, NG * 2, R, lane,
+               [&](int row, const float (&run)[kMaxColsPerLane], bool first, bool last) {
+                 const int k = first ? 0 : (last ? 1 : -1);
+                 if (k < 0) {
+#pragma unroll
+                   for (int q = 0; q < kMaxColsPerLane; ++q) {
+                     const int col = lane + 32 * q;
+                     if (col < R) a.out[(int64_t)row * R + col] = run[q];
+                   }
+                 } else {
+                   if (lane == 0) w_row[warp * 2 + k] = row;
+#pragma unroll
+                   for (int q = 0; q < kMaxColsPerLane; ++q) {
+                     const int col = lane + 32 * q;
+                     if (col < R) w_val[(size_t)(warp * 2 + k) * R + col] = run[q];
+                   }
+                 }
+               });
+  }
+  __syncthreads();
+
+  // Level 2: warp 0 merges the warps.  The CTA's first run may have started in
+  // an earlier CTA, its last run may continue in a later one.
+  if (warp == 0) {
+    int first_row = -1, last_row = -1;
+    for (int e = 0; e < kWalkWarps * 2; ++e) {
+      const int r = w_row[e];
+      if (r >= 0) { if (first_row < 0) first_row = r; last_row = r; }
+    }
+    bool first_partial = false, last_partial = false;
+    if (first_row >= 0) {
+      // rows of the first and last run: where do they begin and end?
+      const int64_t fb = a.fiber_ptr[first_row];
+      const int64_t le = a.fiber_ptr[last_row + 1];
+      first_partial = a.nz_ptr[fb] < cta_p0;
+      last_partial = a.nz_ptr[le] > cta_p1;
+    }
+    if (lane == 0) {
+      a.carry_row[blockIdx.x * 2] = -1;
+      a.carry_row[blockIdx.x * 2 + 1] = -1;
+    }
+    __syncwarp();
+    merge_runs(w_row, w_val, kWalkWarps * 2, R, lane,
+               [&](int row, const float (&run)[kMaxColsPerLane], bool first, bool last) {
+                 const bool partial = (first && first_partial) || (last && last_partial);
+                 if (!partial) {
+#pragma unroll
+                   for (int q = 0; q < kMaxColsPerLane; ++q) {
+                     const int col = lane + 32 * q;
+                     if (col < R) a.out[(int64_t)row * R + col] = run[q];
+                   }
+                 } else {
+                   const int k = (first && first_partial) ? 0 : 1;
+                   if (lane == 0) a.carry_row[blockIdx.x * 2 + k] = row;
+#pragma unroll
+                   for (int q = 0; q < kMaxColsPerLane; ++q) {
+                     const int col = lane + 32 * q;
+                     if (col < R) a.carry[((int64_t)blockIdx.x * 2 + k) * R + col] = run[q];
+                   }
+                 }
+               });
+  }
+}
+
+// Launch one walk configuration (defined in the instantiation units).
+template <typename T>
+cudaError_t launch_walk(int vec, int G, const MttkrpParams& a, int64_t ncta, size_t smem,
+                        cudaStream_t s);
+
+}  // namespace dfacto

@@ -1,0 +1,30 @@
+// mttkrp_bf16.cu -- instantiations of the MTTKRP walk for __nv_bfloat16 factors.
+#include "mttkrp.cuh"
+
+namespace dfacto {
+
+template <int VEC, int G>
+static cudaError_t go(const MttkrpParams& a, int64_t ncta, size_t smem, cudaStream_t s) {
+  auto k = mttkrp_walk<__nv_bfloat16, VEC, G>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<(unsigned)ncta, kWalkWarps * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_walk<__nv_bfloat16>(int vec, int G, const MttkrpParams& a, int64_t ncta, size_t smem,
+                              cudaStream_t s) {
+#define DF_CASE(V, GG) \
+  if (vec == V && G == GG) return go<V, GG>(a, ncta, smem, s);
+  DF_CASE(1, 1) DF_CASE(1, 2) DF_CASE(1, 4) DF_CASE(1, 8) DF_CASE(1, 16) DF_CASE(1, 32)
+  DF_CASE(2, 1) DF_CASE(2, 2) DF_CASE(2, 4) DF_CASE(2, 8) DF_CASE(2, 16) DF_CASE(2, 32)
+  DF_CASE(4, 1) DF_CASE(4, 2) DF_CASE(4, 4) DF_CASE(4, 8) DF_CASE(4, 16) DF_CASE(4, 32)
+  DF_CASE(8, 1) DF_CASE(8, 2) DF_CASE(8, 4) DF_CASE(8, 8) DF_CASE(8, 16)
+#undef DF_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace dfacto

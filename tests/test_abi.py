@@ -1,0 +1,95 @@
+"""The C-ABI library builds, loads, and exports every symbol include/dfacto.h
+declares; the ctypes structs match the C layouts.  No GPU needed: nothing here
+launches a kernel."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dfacto.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1406_4519_gb300 import build_lib, dfacto
+    build_lib.build()
+    return dfacto.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dfacto_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("dfacto_build", "dfacto_mttkrp", "dfacto_als_iter", "dfacto_gd_iter",
+                     "dfacto_fit", "dfacto_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1406_4519_gb300 import dfacto
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in dfacto.SIGNATURES, "binding lacks " + name
+
+
+def test_struct_layouts_match_header(tmp_path, lib):
+    from paper_1406_4519_gb300 import dfacto
+    prog = tmp_path / "layout.c"
+    prog.write_text('''
+#include <stdio.h>
+#include <stddef.h>
+#include "dfacto.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\\n", sizeof(dfacto_options), offsetof(dfacto_options, lambda_reg),
+         offsetof(dfacto_options, seg_nnz), offsetof(dfacto_options, vec));
+  printf("%zu %zu %zu %zu\\n", sizeof(dfacto_info), offsetof(dfacto_info, nnz),
+         offsetof(dfacto_info, norm_x2), offsetof(dfacto_info, vec));
+  printf("%zu %zu\\n", sizeof(dfacto_csr_view), offsetof(dfacto_csr_view, nz_val));
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    got = subprocess.check_output([str(exe)]).decode().split()
+    want = [ctypes.sizeof(dfacto.dfacto_options), dfacto.dfacto_options.lambda_reg.offset,
+            dfacto.dfacto_options.seg_nnz.offset, dfacto.dfacto_options.vec.offset,
+            ctypes.sizeof(dfacto.dfacto_info), dfacto.dfacto_info.nnz.offset,
+            dfacto.dfacto_info.norm_x2.offset, dfacto.dfacto_info.vec.offset,
+            ctypes.sizeof(dfacto.dfacto_csr_view), dfacto.dfacto_csr_view.nz_val.offset]
+    assert [int(x) for x in got] == want
+
+
+def test_host_side_argument_checks(lib):
+    """Invalid arguments are rejected before any device work."""
+    from paper_1406_4519_gb300 import dfacto
+    out = ctypes.c_void_p()
+    dims = (ctypes.c_int32 * 3)(2, 2, 2)
+    assert lib.dfacto_build(None, None, 0, dims, None, None, None) == dfacto.EINVAL
+    bad = (ctypes.c_int32 * 3)(2, 0, 2)
+    assert lib.dfacto_build(None, None, 0, bad, None, None, ctypes.byref(out)) == dfacto.EINVAL
+    assert lib.dfacto_build(None, None, -1, dims, None, None, ctypes.byref(out)) == dfacto.EINVAL
+    opt = dfacto.dfacto_options_init(0)
+    assert lib.dfacto_build(None, None, 0, dims, ctypes.byref(opt), None,
+                            ctypes.byref(out)) == dfacto.EINVAL
+    opt = dfacto.dfacto_options_init(33)  # > 32 and not a multiple of 4
+    assert lib.dfacto_build(None, None, 0, dims, ctypes.byref(opt), None,
+                            ctypes.byref(out)) == dfacto.EINVAL
+    opt = dfacto.dfacto_options_init(10, vec=4)  # 4 does not divide 10
+    assert lib.dfacto_build(None, None, 0, dims, ctypes.byref(opt), None,
+                            ctypes.byref(out)) == dfacto.EINVAL
+    opt = dfacto.dfacto_options_init(8, lambda_reg=-1.0)
+    assert lib.dfacto_build(None, None, 0, dims, ctypes.byref(opt), None,
+                            ctypes.byref(out)) == dfacto.EINVAL
+    assert out.value is None
+    for fn in ("dfacto_mttkrp", "dfacto_als_iter", "dfacto_fit", "dfacto_sync"):
+        args = {"dfacto_mttkrp": (None, 0, None), "dfacto_als_iter": (None, None),
+                "dfacto_fit": (None, None), "dfacto_sync": (None,)}[fn]
+        assert getattr(lib, fn)(*args) == dfacto.EINVAL
+    assert lib.dfacto_status_str(dfacto.EDUP) == b"duplicate coordinate"
