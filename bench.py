@@ -1,0 +1,434 @@
+#!/usr/bin/env python
+"""Benchmark of the DFacTo hot path on one GB300 (or N replicas under torchrun).
+
+Workload (default, "c2"): a 1,000,000 x 500,000 x 200,000 sparse tensor with
+50,000,000 unique nonzeros whose coordinates are Zipf(1.2) in every mode,
+values = a planted rank-32 CP model (N(0,1) factors) plus 1% Gaussian noise,
+rank R = 32, FP32 factors, N(0,1) starting factors.  Synthetic, seeded; the
+paper's real datasets are not available and this stands in for their shape and
+power-law skew.
+
+One step = one DFacTo-ALS sweep (three MTTKRPs with the Gram-Hadamard solve,
+normalisation, and the FP64 fit), inputs resident in HBM.  The CSR copies
+(~1.2 GB) exceed the 129 MB L2, so no flush is needed between steps.  The JSON
+line also carries the GD step rate, the per-mode MTTKRP bandwidth against the
+measured HBM peak (roofline), an end-to-end rate through the C ABI from pinned
+host buffers, and the FP64 CPU oracle timed on a bounded sample.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ALS iter/s"
+WORKLOADS = {
+    "c2": dict(desc="Zipf(1.2) 1000000x500000x200000, 50M unique nnz, planted rank-32 CP + 1% "
+                    "noise, R=32, N(0,1) init",
+               dims=[1_000_000, 500_000, 200_000], nnz=50_000_000, zipf=[1.2, 1.2, 1.2],
+               values="cp", R=32, seed=14064521),
+    "c1": dict(desc="uniform 200x150x100, 10k unique nnz, U(0,1) values, R=10, N(0,1) init",
+               dims=[200, 150, 100], nnz=10_000, zipf=None, values="uniform", R=10,
+               seed=14064520),
+}
+CPU_PHI = 0.1              # cpu_baseline: replica scaled by this factor (~10-30 s)
+REF_BUDGET_S = 120.0       # reference arm: target wall time of all W + K steps
+ORACLE_FULL_S_GUESS = 50.0  # rough oracle seconds per full-size sweep, sizes the replica
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while a measured region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        self.lines += [ln for ln in out.splitlines() if ln.strip()]
+        self.proc = None
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_from_profile(kernel_sha: str):
+    """DRAM bytes per launch of the MTTKRP walk from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "mttkrp_walk_c2.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel source sha256: ([0-9a-f]{64})", text)
+    t = re.search(r"traffic per launch \(bytes, mean of modes\): ([0-9.e+]+)", text)
+    if not m or not t or m.group(1) != kernel_sha:
+        return None
+    return float(t.group(1))
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for name in ("mttkrp.cuh", "mttkrp.cu", "device.cuh"):
+        with open(os.path.join(ROOT, "paper_1406_4519_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def scaled_replica(wl, phi):
+    """The workload scaled by phi: every dimension and the nonzero count times
+    phi, same distributions, same rank."""
+    dims = [max(1, int(round(d * phi))) for d in wl["dims"]]
+    nnz = max(1, int(round(wl["nnz"] * phi)))
+    return dims, nnz
+
+
+def make_replica(wl, phi, device):
+    from paper_1406_4519_gb300 import synth
+    dims, nnz = scaled_replica(wl, phi)
+    if wl["zipf"]:
+        idx, val = synth.zipf_tensor(dims, nnz, wl["zipf"], seed=wl["seed"], device=device,
+                                     values=wl["values"], R_true=wl["R"])
+    else:
+        idx, val = synth.uniform_tensor(dims, nnz, seed=wl["seed"], device=device)
+    F0 = [f.double().cpu().numpy() for f in
+          synth.normal_factors(dims, wl["R"], seed=wl["seed"] + 1, device=device)]
+    return dims, idx.cpu().numpy(), val.cpu().numpy(), F0
+
+
+def oracle_sweep_seconds(dims, idx_np, val_np, F0):
+    """Wall time of one FP64 oracle ALS sweep (three factor updates + fit)."""
+    import oracle
+    t = oracle.Tensor(idx_np, val_np, dims)
+    t0 = time.perf_counter()
+    oracle.als_sweep(t, F0)
+    return time.perf_counter() - t0
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    n_steps = args.steps + args.warmup
+    phi = min(CPU_PHI, max(1.0 / 400, REF_BUDGET_S / (n_steps * ORACLE_FULL_S_GUESS)))
+    if wl["nnz"] * phi < 1000:
+        phi = 1.0 if wl["nnz"] <= 100_000 else phi
+    dims, idx_np, val_np, F0 = make_replica(wl, phi, "cpu")
+    for _ in range(args.warmup):
+        oracle_sweep_seconds(dims, idx_np, val_np, F0)
+    total = 0.0
+    for _ in range(args.steps):
+        total += oracle_sweep_seconds(dims, idx_np, val_np, F0) / phi
+    value = args.steps / total
+    sample = ("one FP64 ALS sweep per step on the workload scaled by phi = %.4g (dims %s, %d "
+              "nnz, same distributions and R), time / phi" % (phi, dims, val_np.shape[0]))
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s",
+          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+          "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+          "config": {"workload": wl["desc"], "dims": wl["dims"], "nnz": wl["nnz"], "rank": wl["R"]},
+          "cpu_baseline": {"value": value, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                           "sample": sample},
+          "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0,
+                  "d2h_bytes_per_step": 0}})
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+
+def algorithmic_bytes(info, uniq, dims, R, elem):
+    """Bytes one MTTKRP of mode n must move: the nonzero stream (nz_idx, nz_val),
+    the fiber stream (fiber_idx, nz_ptr), row(M^r), each touched factor row
+    once, and the output."""
+    out = []
+    for n in range(3):
+        o, i_, f = n, (n + 1) % 3, (n + 2) % 3
+        b = (8 * info.nnz + 12 * info.nfib[n] + 8 * (dims[o] + 1)
+             + elem * R * (uniq[i_] + uniq[f]) + 4 * R * dims[o])
+        out.append(b)
+    return out
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1406_4519_gb300 import dfacto, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = WORKLOADS[args.workload]
+    dims, R = wl["dims"], wl["R"]
+    dtype = dfacto.BF16 if args.dtype == "bf16" else dfacto.F32
+    elem = 2 if args.dtype == "bf16" else 4
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # -- input (seeded, synthetic, generated on the device) --------------------
+    if wl["zipf"]:
+        idx, val = synth.zipf_tensor(dims, wl["nnz"], wl["zipf"], seed=wl["seed"], device=dev,
+                                     values=wl["values"], R_true=wl["R"])
+    else:
+        idx, val = synth.uniform_tensor(dims, wl["nnz"], seed=wl["seed"], device=dev)
+    F0 = synth.normal_factors(dims, R, seed=wl["seed"] + 1, device=dev)
+    uniq = [int(torch.unique(idx[m]).numel()) for m in range(3)]
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    t = dfacto.Tensor(idx, val, dims, rank=R, factor_dtype=dtype, stream=stream)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    info = t.info()
+    t.set_factors(F0)
+
+    sampler = ClockSampler(local_rank)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    # -- ALS: warm-up, then K timed sweeps -------------------------------------
+    for _ in range(args.warmup):
+        t.als_iter(want_fit=False)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = dfacto.dfacto_launch_count()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    for _ in range(args.steps):
+        t.als_iter(want_fit=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = dfacto.dfacto_launch_count() - launches0
+    barrier()
+    torch.cuda.synchronize()
+    als_ms = e0.elapsed_time(e1) / args.steps
+    als_ms_max = max_over_ranks(als_ms)
+    st, fit = t.als_iter(want_fit=True)
+
+    # -- GD: warm-up, then K timed steps ----------------------------------------
+    tg = dfacto.Tensor(idx, val, dims, rank=R, factor_dtype=dtype, stream=stream)
+    tg.set_factors(F0)
+    for _ in range(args.warmup):
+        tg.gd_iter(want=False)
+    torch.cuda.synchronize()
+    g0, g1 = ev(), ev()
+    g0.record(stream)
+    for _ in range(args.steps):
+        tg.gd_iter(want=False)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    gd_ms = g0.elapsed_time(g1) / args.steps
+    st_gd, loss, alpha = tg.gd_iter(want=True)
+    del tg
+
+    # -- MTTKRP per mode (the dominant kernel) ----------------------------------
+    out = torch.empty(max(dims), R, dtype=torch.float32, device=dev)
+    mode_ms = []
+    for mode in range(3):
+        o = out[:dims[mode]]
+        for _ in range(args.warmup):
+            t.mttkrp(mode, o)
+        m0, m1 = ev(), ev()
+        m0.record(stream)
+        for _ in range(args.steps):
+            t.mttkrp(mode, o)
+        m1.record(stream)
+        torch.cuda.synchronize()
+        mode_ms.append(m0.elapsed_time(m1) / args.steps)
+    sampler.stop()
+    alg = algorithmic_bytes(info, uniq, dims, R, elem)
+    peak, peak_kind = measured_peaks()
+    achieved = sum(alg) / (sum(mode_ms) * 1e-3) / 1e9
+    sha = kernel_sha()
+
+    # -- end to end through the C ABI from pinned host buffers -------------------
+    e2e = None
+    if not args.no_e2e:
+        idx_h = idx.cpu().pin_memory()
+        val_h = val.cpu().pin_memory()
+        F0_h = [f.cpu().pin_memory() for f in F0]
+        Fout_h = [torch.empty(d, R, dtype=torch.float32).pin_memory() for d in dims]
+        n_e2e = max(1, min(args.steps, 5))
+
+        def e2e_step():
+            h = dfacto.Tensor(idx_h, val_h, dims, rank=R, factor_dtype=dtype, stream=stream)
+            h.set_factors(F0_h)
+            h.als_iter(want_fit=True)
+            for m in range(3):
+                dfacto.dfacto_get_factors(h.h, m, Fout_h[m])
+            del h
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / n_e2e)
+        fac = 4 * R * sum(dims)
+        e2e = {"value": world / e2e_s, "unit": "iter/s",
+               "h2d_bytes_per_step": 16 * wl["nnz"] + fac, "d2h_bytes_per_step": fac + 8,
+               "steps": n_e2e,
+               "what": "per step: dfacto_build from pinned host COO, set_factors from host, one "
+                       "ALS sweep with fit read-back, get_factors to pinned host"}
+
+    # -- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        phi = 1.0 if wl["nnz"] <= 100_000 else CPU_PHI
+        rdims, idx_np, val_np, F0_np = make_replica(wl, phi, dev)
+        t_s = oracle_sweep_seconds(rdims, idx_np, val_np, F0_np)
+        cpu = {"value": phi / t_s, "unit": "iter/s", "cores": 1, "kind": "oracle",
+               "sample": "one FP64 ALS sweep on the workload scaled by phi = %g (dims %s, %d "
+                         "nnz, same distributions and R): %.1f s, time / phi" %
+                         (phi, rdims, val_np.shape[0], t_s)}
+
+    if rank != 0:
+        return
+    clocks = sampler.summary()
+    emit({
+        "metric": METRIC, "value": world * 1e3 / als_ms_max, "unit": "iter/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": als_ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if dtype == dfacto.F32 else "bf16-storage/f32",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "dims": dims, "nnz": wl["nnz"], "rank": R,
+                   "factor_storage": args.dtype, "nfib": list(info.nfib),
+                   "l2": "no flush: inputs (CSR ~%.1f GB) exceed the 129 MB L2" %
+                         (sum(8 * info.nnz + 16 * x for x in info.nfib) / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic_from_profile(sha),
+                     "kernel": "mttkrp_walk (+ carry fix-up), mean over the three modes",
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_mode": alg, "ms_per_mode": mode_ms,
+                     "gbs_per_mode": [b / (m * 1e-3) / 1e9 for b, m in zip(alg, mode_ms)]},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks,
+        "gd_iter_per_s": 1e3 / gd_ms, "gd_ms": gd_ms, "gd_alpha": alpha, "gd_loss": loss,
+        "als_fit": fit, "build_s": build_s,
+    })
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -155,6 +155,12 @@ void dfacto_destroy(dfacto_t* h);
 /* One-line description of the last failure on the handle ("" if none). */
 const char* dfacto_last_error(const dfacto_t* h);
 
+/*
+ * Number of CUDA kernels this library has launched in this process so far
+ * (all handles).  The difference around a call is that call's launch count.
+ */
+int64_t dfacto_launch_count(void);
+
 /* Sizes of the built tensor (host struct). */
 dfacto_status dfacto_get_info(dfacto_t* h, dfacto_info* info);
 

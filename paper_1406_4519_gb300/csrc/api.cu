@@ -12,6 +12,8 @@
 
 namespace dfacto {
 
+std::atomic<long long> g_launches{0};
+
 dfacto_status fail(dfacto_t* h, dfacto_status s, const std::string& what) {
   if (h) h->err = what;
   return s;
@@ -79,10 +81,14 @@ __global__ void convert_kernel(const S* __restrict__ src, D* __restrict__ dst, i
 template <typename S>
 cudaError_t convert_from(const S* src, void* dst, int dst_dtype, int64_t n, cudaStream_t s) {
   const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
-  if (dst_dtype == DFACTO_F32) convert_kernel<S, float><<<nb, 256, 0, s>>>(src, (float*)dst, n);
-  else if (dst_dtype == DFACTO_BF16)
+  if (dst_dtype == DFACTO_F32) {
+    convert_kernel<S, float><<<nb, 256, 0, s>>>(src, (float*)dst, n);
+  } else if (dst_dtype == DFACTO_BF16) {
     convert_kernel<S, __nv_bfloat16><<<nb, 256, 0, s>>>(src, (__nv_bfloat16*)dst, n);
-  else convert_kernel<S, double><<<nb, 256, 0, s>>>(src, (double*)dst, n);
+  } else {
+    convert_kernel<S, double><<<nb, 256, 0, s>>>(src, (double*)dst, n);
+  }
+  DF_COUNT();
   return cudaGetLastError();
 }
 
@@ -224,6 +230,8 @@ void dfacto_destroy(dfacto_t* h) {
 
 const char* dfacto_last_error(const dfacto_t* h) { return h ? h->err.c_str() : ""; }
 
+int64_t dfacto_launch_count(void) { return (int64_t)g_launches.load(); }
+
 dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, const int32_t dims[3],
                            const dfacto_options* opt_in, void* stream, dfacto_t** out) {
   if (!out) return DFACTO_EINVAL;
@@ -285,7 +293,7 @@ dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, co
   for (int m = 0; m < 3; ++m)
     if (cudaMemsetAsync(h->F[m], 0, elem_size(h->dtype) * (size_t)dims[m] * R, s) != cudaSuccess)
       return bail(DFACTO_ECUDA);
-  fill_double<<<1, 128, 0, s>>>(h->lambda, R, 1.0);
+  fill_double<<<1, 128, 0, s>>>(h->lambda, R, 1.0); DF_COUNT();
 
   // COO on the device.
   const int32_t* d_idx = idx;

@@ -280,11 +280,11 @@ cudaError_t radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, i
   uint32_t *vi = v0, *vo = v1;
   for (int pass = 0; pass < passes && e == cudaSuccess; ++pass) {
     const int shift = 8 * pass;
-    radix_hist<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n, shift, cnt, ntiles);
+    radix_hist<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n, shift, cnt, ntiles); DF_COUNT();
     e = cudaGetLastError();
     if (e == cudaSuccess) e = exclusive_scan_i32(cnt, cnt, kDigits * ntiles, s);
     if (e == cudaSuccess) {
-      radix_scatter<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, cnt, ntiles);
+      radix_scatter<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, cnt, ntiles); DF_COUNT();
       e = cudaGetLastError();
     }
     std::swap(ki, ko);
@@ -310,7 +310,7 @@ dfacto_status ensure_segments(dfacto_t* h, int mode) {
                             sizeof(int32_t) * (size_t)std::max<int64_t>(M.nseg, 1));
   if (st != DFACTO_OK) return st;
   if (M.nseg > 0) {
-    segment_starts<<<grid_for(M.nseg), 256, 0, h->stream>>>(M.nz_ptr, M.nfib, M.nseg, seg, M.seg_fib);
+    segment_starts<<<grid_for(M.nseg), 256, 0, h->stream>>>(M.nz_ptr, M.nfib, M.nseg, seg, M.seg_fib); DF_COUNT();
     DF_CUDA(h, cudaGetLastError());
   }
   M.seg_fib_for = seg;
@@ -323,7 +323,7 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
   DF_CUDA(h, cudaMemsetAsync(h->flags, 0, sizeof(int32_t) * kNumFlags, s));
   if (n > 0) {
     check_range<<<grid_for(n), 256, 0, s>>>(d_idx, n, h->dims[0], h->dims[1], h->dims[2],
-                                            h->flags + kFlagRange);
+                                            h->flags + kFlagRange); DF_COUNT();
     DF_CUDA(h, cudaGetLastError());
     DF_CUDA(h, cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int32_t) * kNumFlags,
                                cudaMemcpyDeviceToHost, s));
@@ -333,8 +333,8 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
   // ||X||^2 once (FP64).
   {
     const unsigned nb = grid_for(n, 256, 1024);
-    sumsq_partials<<<nb, 256, 0, s>>>(d_val, n, h->partials);
-    sum_partials<<<1, 32, 0, s>>>(h->partials, (int)nb, h->scal + kNormX2);
+    sumsq_partials<<<nb, 256, 0, s>>>(d_val, n, h->partials); DF_COUNT();
+    sum_partials<<<1, 32, 0, s>>>(h->partials, (int)nb, h->scal + kNormX2); DF_COUNT();
     DF_CUDA(h, cudaGetLastError());
   }
 
@@ -395,11 +395,11 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
     }
     bool alt = false, alt2 = false;
     if (!wide) {
-      make_keys64<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, M.in, bf, bi, k0, v0);
+      make_keys64<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, M.in, bf, bi, k0, v0); DF_COUNT();
       e = cudaGetLastError();
       if (e == cudaSuccess) e = radix_sort(k0, v0, k1, v1, n, bo + bf + bi, s, &alt);
     } else {
-      make_keys_in<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.in, k0, v0);
+      make_keys_in<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.in, k0, v0); DF_COUNT();
       e = cudaGetLastError();
       if (e == cudaSuccess) e = radix_sort(k0, v0, k1, v1, n, bi, s, &alt);
       uint64_t* kk = alt ? k1 : k0;
@@ -407,7 +407,7 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
       uint64_t* ko = alt ? k0 : k1;
       uint32_t* vo = alt ? v0 : v1;
       if (e == cudaSuccess) {
-        make_keys_of<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, bf, vv, kk);
+        make_keys_of<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, bf, vv, kk); DF_COUNT();
         e = cudaGetLastError();
       }
       if (e == cudaSuccess) e = radix_sort(kk, vv, ko, vo, n, bo + bf, s, &alt2);
@@ -420,7 +420,7 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
     const uint64_t* key = alt ? k1 : k0;
     const uint32_t* perm = alt ? v1 : v0;
     segment_flags<<<grid_for(n), 256, 0, s>>>(key, perm, n, bi, wide, d_idx, M.in, d_val, head,
-                                             M.nz_idx, M.nz_val, h->flags + kFlagDup);
+                                             M.nz_idx, M.nz_val, h->flags + kFlagDup); DF_COUNT();
     e = cudaGetLastError();
     if (e == cudaSuccess) e = exclusive_scan_i32(head, fid, n, s);
     int32_t last[2] = {0, 0};
@@ -442,8 +442,8 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
       return st;
     }
     scatter_fibers<<<grid_for(n), 256, 0, s>>>(key, perm, n, bf, bi, wide, head, fid, M.nz_ptr,
-                                              M.fiber_idx, M.fiber_row, M.nfib);
-    row_pointers<<<grid_for(M.dim_o + 1), 256, 0, s>>>(M.fiber_row, M.nfib, M.dim_o, M.fiber_ptr);
+                                              M.fiber_idx, M.fiber_row, M.nfib); DF_COUNT();
+    row_pointers<<<grid_for(M.dim_o + 1), 256, 0, s>>>(M.fiber_row, M.nfib, M.dim_o, M.fiber_ptr); DF_COUNT();
     e = cudaGetLastError();
     if (e != cudaSuccess) {
       cleanup();

@@ -604,16 +604,18 @@ dfacto_status cross_gram(dfacto_t* h, const TX* X, const TY* Y, int64_t rows, do
   const size_t smem = sizeof(float) * 2 * (size_t)trows * R;
   if ((int64_t)nb * R * R > h->partials_cap) return fail(h, DFACTO_EINTERNAL, "partials too small");
   const int per = (R * R + kRowThreads - 1) / kRowThreads;
-  if (per <= 1)
+  if (per <= 1) {
     cross_gram_partials<TX, TY, 1><<<nb, kRowThreads, smem, h->stream>>>(X, Y, rows, R, h->partials);
-  else if (per <= 4)
+  } else if (per <= 4) {
     cross_gram_partials<TX, TY, 4><<<nb, kRowThreads, smem, h->stream>>>(X, Y, rows, R, h->partials);
-  else if (per <= 16)
+  } else if (per <= 16) {
     cross_gram_partials<TX, TY, 16><<<nb, kRowThreads, smem, h->stream>>>(X, Y, rows, R, h->partials);
-  else
+  } else {
     cross_gram_partials<TX, TY, 64><<<nb, kRowThreads, smem, h->stream>>>(X, Y, rows, R, h->partials);
+  }
+  DF_COUNT();
   reduce_partials<<<(R * R + 255) / 256, 256, 0, h->stream>>>(h->partials, (int)nb, R * R, R,
-                                                               symmetrize, out);
+                                                               symmetrize, out); DF_COUNT();
   DF_CUDA(h, cudaGetLastError());
   return DFACTO_OK;
 }
@@ -643,7 +645,7 @@ dfacto_status als_mode_T(dfacto_t* h, int mode) {
   for (int m : {M.f, M.in})
     if (!h->gram_valid[m] && (st = gram_of_factor(h, m)) != DFACTO_OK) return st;
   gamma_inverse<<<1, 256, 0, s>>>(h->gram[M.f], h->gram[M.in], R, h->lambda_reg, h->W, h->W32,
-                                  h->flags + kFlagSingular, h->rr_work);
+                                  h->flags + kFlagSingular, h->rr_work); DF_COUNT();
   DF_CUDA(h, cudaGetLastError());
   if ((st = mttkrp_launch(h, mode, h->N)) != DFACTO_OK) return st;
   const int64_t rows = M.dim_o;
@@ -651,12 +653,12 @@ dfacto_status als_mode_T(dfacto_t* h, int mode) {
   const size_t smem = sizeof(float) * R * R;
   allow_smem(als_colnorm_partials, smem);
   allow_smem(als_normalize<T>, smem);
-  als_colnorm_partials<<<nb, kRowThreads, smem, s>>>(h->N, h->W32, rows, R, h->partials);
-  finish_lambda<<<1, 128, 0, s>>>(h->partials, (int)nb, R, h->lambda, h->inv_lambda);
+  als_colnorm_partials<<<nb, kRowThreads, smem, s>>>(h->N, h->W32, rows, R, h->partials); DF_COUNT();
+  finish_lambda<<<1, 128, 0, s>>>(h->partials, (int)nb, R, h->lambda, h->inv_lambda); DF_COUNT();
   const bool last = (mode == 2);
   als_normalize<T><<<nb, kRowThreads, smem, s>>>(h->N, h->W32, h->inv_lambda, rows, R,
                                                  static_cast<T*>(h->F[mode]),
-                                                 last ? h->partials : nullptr);
+                                                 last ? h->partials : nullptr); DF_COUNT();
   DF_CUDA(h, cudaGetLastError());
   h->gram_valid[mode] = false;
   if (last) {
@@ -676,7 +678,7 @@ dfacto_status als_mode(dfacto_t* h, int mode) {
 
 dfacto_status als_fit(dfacto_t* h) {
   fit_from_parts<<<1, 256, 0, h->stream>>>(h->ipart, h->ipart_blocks, h->R, h->lambda, h->gram[0],
-                                           h->gram[1], h->gram[2], h->scal);
+                                           h->gram[1], h->gram[2], h->scal); DF_COUNT();
   DF_CUDA(h, cudaGetLastError());
   return DFACTO_OK;
 }
@@ -729,7 +731,7 @@ dfacto_status fit_direct_T(dfacto_t* h) {
   const int64_t rows = h->dims[2];
   const unsigned nb = row_blocks(rows);
   rows_dot_partials<T><<<nb, kRowThreads, 0, h->stream>>>(h->N, static_cast<const T*>(h->F[2]),
-                                                          rows, h->R, h->ipart);
+                                                          rows, h->R, h->ipart); DF_COUNT();
   DF_CUDA(h, cudaGetLastError());
   h->ipart_blocks = (int)nb;
   return als_fit(h);
@@ -758,16 +760,16 @@ dfacto_status gd_step_T(dfacto_t* h) {
   DF_CUDA(h, cudaMemsetAsync(h->scal + kG2, 0, sizeof(double), s));
   for (int mode = 0; mode < 3; ++mode) {
     const ModeCSR& M = h->m[mode];
-    hadamard_gamma<<<1, 256, 0, s>>>(h->gram[M.f], h->gram[M.in], R, h->lambda_reg, h->W, h->W32);
+    hadamard_gamma<<<1, 256, 0, s>>>(h->gram[M.f], h->gram[M.in], R, h->lambda_reg, h->W, h->W32); DF_COUNT();
     if ((st = mttkrp_launch(h, mode, h->N)) != DFACTO_OK) return st;
     const int64_t rows = M.dim_o;
     const unsigned nb = row_blocks(rows);
     allow_smem(gd_gradient_rows<T>, sizeof(float) * R * R);
     gd_gradient_rows<T><<<nb, kRowThreads, sizeof(float) * R * R, s>>>(
-        h->N, static_cast<const T*>(h->F[mode]), h->W32, rows, R, h->grad[mode], h->partials);
+        h->N, static_cast<const T*>(h->F[mode]), h->W32, rows, R, h->grad[mode], h->partials); DF_COUNT();
     const int tlin = mode == 0 ? kT100 : (mode == 1 ? kT010 : kT001);
     reduce_scalars<<<1, 32, 0, s>>>(h->partials, (int)nb, 3, h->scal, kG2, tlin,
-                                    mode == 0 ? kT000 : -1);
+                                    mode == 0 ? kT000 : -1); DF_COUNT();
     DF_CUDA(h, cudaGetLastError());
   }
   // R x R matrices of the polynomial: P0 = F^T F, P1 = F^T G + G^T F, P2 = G^T G.
@@ -782,10 +784,10 @@ dfacto_status gd_step_T(dfacto_t* h) {
       return st;
   }
   if ((st = dual_pass(h)) != DFACTO_OK) return st;
-  gd_line_search<<<1, 256, 0, s>>>(h->gd_mats, R, h->lambda_reg, h->scal, h->flags + kFlagLsFail);
+  gd_line_search<<<1, 256, 0, s>>>(h->gd_mats, R, h->lambda_reg, h->scal, h->flags + kFlagLsFail); DF_COUNT();
   for (int m = 0; m < 3; ++m) {
     const int64_t n = (int64_t)h->dims[m] * R;
-    gd_update<T><<<row_blocks(n, 1024), 256, 0, s>>>(static_cast<T*>(h->F[m]), h->grad[m], n, h->scal);
+    gd_update<T><<<row_blocks(n, 1024), 256, 0, s>>>(static_cast<T*>(h->F[m]), h->grad[m], n, h->scal); DF_COUNT();
     h->gram_valid[m] = false;
   }
   DF_CUDA(h, cudaGetLastError());

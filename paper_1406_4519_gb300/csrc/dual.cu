@@ -157,7 +157,7 @@ __global__ void dual_reduce(const double* __restrict__ part, int64_t ncta, doubl
 
 template <typename T, int VEC, int G>
 cudaError_t go(const DualParams& a, int64_t ncta, cudaStream_t s) {
-  dual_walk<T, VEC, G><<<(unsigned)ncta, kWalkWarps * 32, 0, s>>>(a);
+  dual_walk<T, VEC, G><<<(unsigned)ncta, kWalkWarps * 32, 0, s>>>(a); DF_COUNT();
   return cudaGetLastError();
 }
 
@@ -210,7 +210,7 @@ dfacto_status dual_pass(dfacto_t* h) {
                       ? launch<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, h->stream)
                       : launch<float>(cfg.vec, cfg.G, a, ncta, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "dual_walk launch");
-  dual_reduce<<<1, 32, 0, h->stream>>>(h->partials, ncta, h->scal);
+  dual_reduce<<<1, 32, 0, h->stream>>>(h->partials, ncta, h->scal); DF_COUNT();
   DF_CUDA(h, cudaGetLastError());
   return DFACTO_OK;
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/dfacto.h"
@@ -102,6 +103,10 @@ struct dfacto_handle {
 };
 
 namespace dfacto {
+
+// Kernels launched by this library in this process (dfacto_launch_count).
+extern std::atomic<long long> g_launches;
+#define DF_COUNT() ::dfacto::g_launches.fetch_add(1, std::memory_order_relaxed)
 
 // ---- errors ---------------------------------------------------------------
 dfacto_status fail(dfacto_t* h, dfacto_status s, const std::string& what);

@@ -145,7 +145,7 @@ dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out) {
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(std::max(ncta, zero_blocks), 152 * 16));
   mttkrp_fixup<<<(unsigned)blocks, kFixThreads, 0, h->stream>>>(
       h->carry_row, h->carry, M.fiber_ptr, M.nz_ptr, out, h->R, P, ncta, M.dim_o,
-      h->flags + kFlagInternal);
+      h->flags + kFlagInternal); DF_COUNT();
   DF_CUDA(h, cudaGetLastError());
   return DFACTO_OK;
 }

@@ -10,7 +10,7 @@ static cudaError_t go(const MttkrpParams& a, int64_t ncta, size_t smem, cudaStre
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k<<<(unsigned)ncta, kWalkWarps * 32, smem, s>>>(a);
+  k<<<(unsigned)ncta, kWalkWarps * 32, smem, s>>>(a); DF_COUNT();
   return cudaGetLastError();
 }
 

@@ -76,17 +76,17 @@ cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaS
   if (n <= 0) return cudaSuccess;
   const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
   if (ntiles == 1) {
-    tile_scan<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+    tile_scan<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr); DF_COUNT();
     return cudaGetLastError();
   }
   int32_t* tot = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tot), sizeof(int32_t) * ntiles, s);
   if (e != cudaSuccess) return e;
-  tile_totals<<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, tot);
+  tile_totals<<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, tot); DF_COUNT();
   e = cudaGetLastError();
   if (e == cudaSuccess) e = exclusive_scan_i32(tot, tot, ntiles, s);
   if (e == cudaSuccess) {
-    tile_scan<<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, out, n, tot);
+    tile_scan<<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, out, n, tot); DF_COUNT();
     e = cudaGetLastError();
   }
   cudaError_t e2 = cudaFreeAsync(tot, s);

@@ -61,6 +61,7 @@ SIGNATURES = {
     "dfacto_build": (_I, [_P, _P, _I64, _P, _P, _P, _P]),
     "dfacto_destroy": (None, [_P]),
     "dfacto_last_error": (ctypes.c_char_p, [_P]),
+    "dfacto_launch_count": (ctypes.c_int64, []),
     "dfacto_get_info": (_I, [_P, _P]),
     "dfacto_set_stream": (_I, [_P, _P]),
     "dfacto_sync": (_I, [_P]),
@@ -148,6 +149,10 @@ def dfacto_destroy(h) -> None:
 
 def dfacto_last_error(h) -> str:
     return load().dfacto_last_error(h).decode()
+
+
+def dfacto_launch_count() -> int:
+    return int(load().dfacto_launch_count())
 
 
 def dfacto_get_info(h) -> dfacto_info:
