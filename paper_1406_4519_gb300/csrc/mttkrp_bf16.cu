@@ -6,11 +6,16 @@ namespace dfacto {
 template <int VEC, int G>
 static cudaError_t go(const MttkrpParams& a, int64_t ncta, size_t smem, cudaStream_t s) {
   auto k = mttkrp_walk<__nv_bfloat16, VEC, G>;
-  if (smem > 48 * 1024) {
+  // Opt in to the dynamic shared memory this launch needs (the default limit
+  // is 48 KB including the kernel's static shared memory).
+  static size_t configured = 0;
+  if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    configured = smem;
   }
-  k<<<(unsigned)ncta, kWalkWarps * 32, smem, s>>>(a); DF_COUNT();
+  k<<<(unsigned)ncta, kWalkWarps * 32, smem, s>>>(a);
+  DF_COUNT();
   return cudaGetLastError();
 }
 

@@ -85,7 +85,9 @@ def load(path: str = LIB_PATH):
             raise ImportError("libdfacto.so not found at %s; run __graft_entry__.build()" % path)
         lib = ctypes.CDLL(path)
         for name, (res, args) in SIGNATURES.items():
-            fn = getattr(lib, name)
+            fn = getattr(lib, name, None)
+            if fn is None:
+                raise ImportError("%s does not export %s" % (path, name))
             fn.restype = res
             fn.argtypes = args
         _lib = lib
