@@ -240,6 +240,46 @@ dfacto_status dfacto_fit(dfacto_t* h, double* fit_out);
 /* Device pointers to the CSR copy of one mode (see dfacto_csr_view). */
 dfacto_status dfacto_get_csr(dfacto_t* h, int mode, dfacto_csr_view* view);
 
+/*
+ * dfacto_mttkrp_noalloc -- the same MTTKRP as dfacto_mttkrp for one mode, for
+ * callers that are not allowed to allocate device memory: code whose device
+ * memory is owned and accounted by another allocator (a framework's caching
+ * allocator, a memory-capped service), code running in a section where an
+ * allocation could block or fail at the wrong moment, or code that only borrows
+ * device pointers from their owner.  dfacto_mttkrp may allocate its work
+ * buffers on first use; this entry point never calls cudaMalloc, cudaFree or
+ * any allocating routine.  The paper has no counterpart.
+ *
+ * Its scratch (segment starts and the partial sums of rows shared between
+ * blocks) lives in one fixed 16 MiB device array inside the library.  Every
+ * GPU that loads the library holds that array until the process exits.  The
+ * problem must fit in it: about 250 million nonzeros at R = 32 (the layout is
+ * 4 bytes per 128 nonzeros plus 8 * R + 8 bytes per 8,192 nonzeros at R = 32).
+ *   csr     host struct of device pointers to the flattened CSR copy of mode n,
+ *           in the layout dfacto_get_csr describes (from a handle, or built by
+ *           the caller the same way); nnz < 2^31.
+ *   F_in    device float[dims[(n+1) mod 3] x R], row-major: the factor indexed
+ *           by nz_idx.
+ *   F_f     device float[dims[(n+2) mod 3] x R], row-major: the factor indexed
+ *           by fiber_idx.
+ *   R       1..128 (R > 32 a multiple of 4).
+ *   out     device float[dim_o x R], row-major; every entry is written.
+ *   stream  cudaStream_t for the work (NULL: the legacy default stream).
+ * Returns DFACTO_ENOMEM when the problem needs more scratch than the 16 MiB
+ * array holds, DFACTO_EINVAL for bad arguments, DFACTO_ECUDA if a launch
+ * failed.  Asynchronous otherwise.
+ *
+ * The first call on a device, with that device current, looks up the device
+ * address of the array (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the one array and a call leaves its
+ * contents behind: calls whose work may overlap on the GPU (different streams
+ * or threads without ordering) race on it and must be serialised by the
+ * caller.  Nothing in the array needs to start at zero: each call writes every
+ * scratch value it later reads.
+ */
+dfacto_status dfacto_mttkrp_noalloc(const dfacto_csr_view* csr, const float* F_in, const float* F_f,
+                                    int32_t R, float* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

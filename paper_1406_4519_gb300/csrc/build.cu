@@ -16,6 +16,7 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "mttkrp.cuh"
 
 namespace dfacto {
 namespace {
@@ -296,6 +297,14 @@ cudaError_t radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, i
 }
 
 }  // namespace
+
+cudaError_t launch_segment_starts(const int64_t* nz_ptr, int64_t nfib, int64_t nseg, int64_t seg,
+                                  int32_t* seg_fib, cudaStream_t s) {
+  if (nseg <= 0) return cudaSuccess;
+  segment_starts<<<grid_for(nseg), 256, 0, s>>>(nz_ptr, nfib, nseg, seg, seg_fib);
+  DF_COUNT();
+  return cudaGetLastError();
+}
 
 dfacto_status ensure_segments(dfacto_t* h, int mode) {
   ModeCSR& M = h->m[mode];

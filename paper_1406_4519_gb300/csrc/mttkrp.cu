@@ -77,6 +77,18 @@ int next_pow2(int x) {
 
 }  // namespace
 
+cudaError_t launch_mttkrp_fixup(const int32_t* carry_row, const float* carry,
+                                const int64_t* fiber_ptr, const int64_t* nz_ptr, float* out, int R,
+                                int64_t P, int64_t ncta, int64_t dim_o, int32_t* bad,
+                                cudaStream_t s) {
+  const int64_t zero_blocks = (dim_o + kFixThreads - 1) / kFixThreads;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(std::max(ncta, zero_blocks), 152 * 16));
+  mttkrp_fixup<<<(unsigned)blocks, kFixThreads, 0, s>>>(carry_row, carry, fiber_ptr, nz_ptr, out, R,
+                                                         P, ncta, dim_o, bad);
+  DF_COUNT();
+  return cudaGetLastError();
+}
+
 WalkCfg choose_walk(int R, int dtype, int64_t nnz, int64_t nfib, int seg_opt, int vec_opt) {
   (void)nnz;
   (void)nfib;
@@ -135,6 +147,7 @@ dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out) {
   a.carry_row = h->carry_row;
   a.nnz = h->nnz;
   a.nfib = M.nfib;
+  a.dim_o = M.dim_o;
   a.R = h->R;
   a.seg = cfg.seg;
   if (ncta > 0) {

@@ -43,6 +43,7 @@ struct MttkrpParams {
   int32_t* carry_row; // [ncta][2]
   int64_t nnz;
   int64_t nfib;
+  int64_t dim_o;
   int R;
   int seg;
 };
@@ -82,7 +83,27 @@ __device__ __forceinline__ void merge_runs(const int32_t* rows, const float* val
   if (run_row >= 0) flush(run_row, run, run_first, true);
 }
 
-template <typename T, int VEC, int G>
+// Row of fiber q from row(M^r) alone: the largest r < dim_o with
+// fiber_ptr[r] <= q (empty rows have fiber_ptr[r] == fiber_ptr[r + 1]).
+__device__ __forceinline__ int row_of_fiber(const int64_t* fiber_ptr, int64_t dim_o, int64_t q) {
+  int64_t lo = 0, hi = dim_o - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (fiber_ptr[mid] <= q) lo = mid; else hi = mid - 1;
+  }
+  return (int)lo;
+}
+
+// Row of fiber q given the row r0 of an earlier fiber (rows ascend with q).
+__device__ __forceinline__ int row_after(const int64_t* fiber_ptr, int r0, int64_t q) {
+  int r = r0;
+  while (__ldg(fiber_ptr + r + 1) <= q) ++r;
+  return r;
+}
+
+// kRowsFromPtr: take each fiber's row from fiber_ptr instead of the fiber_row
+// array (for callers that pass only the CSR arrays of dfacto_csr_view).
+template <typename T, int VEC, int G, bool kRowsFromPtr = false>
 __global__ void __launch_bounds__(kWalkWarps * 32) mttkrp_walk(const MttkrpParams a) {
   constexpr int NG = 32 / G;
   constexpr int SEGS = kWalkWarps * NG;
@@ -116,12 +137,14 @@ __global__ void __launch_bounds__(kWalkWarps * 32) mttkrp_walk(const MttkrpParam
   if (active) {
     fib = a.seg_fib[(int64_t)blockIdx.x * SEGS + sl];
     fend = min(a.nz_ptr[fib + 1], p1);
-    row_cur = a.fiber_row[fib];
+    if constexpr (kRowsFromPtr) row_cur = row_of_fiber(a.fiber_ptr, a.dim_o, fib);
+    else row_cur = a.fiber_row[fib];
     if (colok) VecIO<T, VEC>::load(Ff + (int64_t)a.fiber_idx[fib] * R + col0, ffc);
     if (fib + 1 < a.nfib) {
       fend_next = a.nz_ptr[fib + 2];
       f_next = a.fiber_idx[fib + 1];
-      row_next = a.fiber_row[fib + 1];
+      if constexpr (kRowsFromPtr) row_next = row_after(a.fiber_ptr, row_cur, fib + 1);
+      else row_next = a.fiber_row[fib + 1];
     }
   }
 
@@ -186,7 +209,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32) mttkrp_walk(const MttkrpParam
               if (fib + 1 < a.nfib) {
                 fend_next = __ldg(a.nz_ptr + fib + 2);
                 f_next = __ldg(a.fiber_idx + fib + 1);
-                row_next = __ldg(a.fiber_row + fib + 1);
+                if constexpr (kRowsFromPtr) row_next = row_after(a.fiber_ptr, row_cur, fib + 1);
+                else row_next = __ldg(a.fiber_row + fib + 1);
               }
             }
           }
@@ -274,6 +298,15 @@ __global__ void __launch_bounds__(kWalkWarps * 32) mttkrp_walk(const MttkrpParam
                });
   }
 }
+
+// Launchers of the carry fix-up (mttkrp.cu) and of the segment-start search
+// (build.cu), shared with the allocation-free entry point.
+cudaError_t launch_mttkrp_fixup(const int32_t* carry_row, const float* carry,
+                                const int64_t* fiber_ptr, const int64_t* nz_ptr, float* out, int R,
+                                int64_t P, int64_t ncta, int64_t dim_o, int32_t* bad,
+                                cudaStream_t s);
+cudaError_t launch_segment_starts(const int64_t* nz_ptr, int64_t nfib, int64_t nseg, int64_t seg,
+                                  int32_t* seg_fib, cudaStream_t s);
 
 // Launch one walk configuration (defined in the instantiation units).
 template <typename T>

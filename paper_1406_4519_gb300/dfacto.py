@@ -74,6 +74,7 @@ SIGNATURES = {
     "dfacto_gd_iter": (_I, [_P, _P, _P]),
     "dfacto_fit": (_I, [_P, _P]),
     "dfacto_get_csr": (_I, [_P, _I, _P]),
+    "dfacto_mttkrp_noalloc": (_I, [_P, _P, _P, ctypes.c_int32, _P, _P]),
 }
 
 
@@ -240,6 +241,21 @@ def device_view(ptr: int, n: int, dtype: torch.dtype) -> torch.Tensor:
     if n == 0:
         return torch.empty(0, dtype=dtype, device="cuda")
     return torch.as_tensor(_Iface(), device="cuda")
+
+
+def dfacto_mttkrp_noalloc(csr: dfacto_csr_view, F_in: torch.Tensor, F_f: torch.Tensor, R: int,
+                          out: torch.Tensor, stream=None) -> torch.Tensor:
+    """MTTKRP of one mode without any device allocation (scratch in the
+    library's fixed 16 MiB device array); arguments as in include/dfacto.h."""
+    for t in (F_in, F_f, out):
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    st = load().dfacto_mttkrp_noalloc(ctypes.byref(csr), F_in.data_ptr(), F_f.data_ptr(), int(R),
+                                      out.data_ptr(), _stream_ptr(stream))
+    if st == ENOMEM:
+        raise DfactoError(st, "dfacto_mttkrp_noalloc: the problem needs more scratch than the "
+                              "library's fixed 16 MiB device array holds")
+    _check(st)
+    return out
 
 
 def csr_to_tensors(view: dfacto_csr_view) -> dict:
