@@ -210,6 +210,7 @@ void dfacto_destroy(dfacto_t* h) {
     cudaFree(h->gram[m]);
   }
   cudaFree(h->N);
+  cudaFree(h->Fh);
   cudaFree(h->lambda);
   cudaFree(h->inv_lambda);
   cudaFree(h->ipart);
@@ -273,12 +274,13 @@ dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, co
   if ((st = grow_partials(h, std::max<int64_t>(608 * (int64_t)RR, 4096))) != DFACTO_OK) return bail(st);
   if ((st = dalloc(h, (void**)&h->lambda, sizeof(double) * R)) != DFACTO_OK) return bail(st);
   if ((st = dalloc(h, (void**)&h->inv_lambda, sizeof(float) * R)) != DFACTO_OK) return bail(st);
-  if ((st = dalloc(h, (void**)&h->ipart, sizeof(double) * 608 * R)) != DFACTO_OK) return bail(st);
+  if ((st = dalloc(h, (void**)&h->ipart, sizeof(double) * 608 * R)) != DFACTO_OK) return bail(st);  // >= blocks
   if ((st = dalloc(h, (void**)&h->gd_mats, sizeof(double) * 9 * RR)) != DFACTO_OK) return bail(st);
   if ((st = dalloc(h, (void**)&h->W, sizeof(double) * RR)) != DFACTO_OK) return bail(st);
   if ((st = dalloc(h, (void**)&h->rr_work, sizeof(double) * (2 * RR + R))) != DFACTO_OK) return bail(st);
   if ((st = dalloc(h, (void**)&h->W32, sizeof(float) * RR)) != DFACTO_OK) return bail(st);
   if ((st = dalloc(h, (void**)&h->N, sizeof(float) * maxdim * R)) != DFACTO_OK) return bail(st);
+  if ((st = dalloc(h, (void**)&h->Fh, sizeof(float) * maxdim * R)) != DFACTO_OK) return bail(st);
   for (int m = 0; m < 3; ++m) {
     if ((st = dalloc(h, &h->F[m], elem_size(h->dtype) * (size_t)dims[m] * R)) != DFACTO_OK) return bail(st);
     if ((st = dalloc(h, (void**)&h->gram[m], sizeof(double) * RR)) != DFACTO_OK) return bail(st);

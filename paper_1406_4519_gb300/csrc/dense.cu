@@ -4,11 +4,17 @@
 // normalisation and CP weights (Algorithm 2), the fit, and the GD gradient
 // (Eq. gd-A), line search and update (Algorithm 5).
 //
+// Layout of the row passes: a block stages a tile of kTile rows in shared
+// memory and each thread produces four consecutive columns of one row at a
+// time; Grams use 4 x 4 register blocks over the staged rows.  These passes are
+// bound by HBM (one read and one write of a dim x R matrix).
+//
 // Precision: factor rows are read in their storage type and multiplied in
-// FP32; every reduction that feeds a Gram, a norm, the fit or the GD objective
-// folds FP32 partials of at most kFold rows into FP64, and all R x R work is
-// FP64.  Reductions use fixed per-block partials summed in block order, so
-// results are bitwise reproducible.
+// FP32; partial sums over at most kFoldTiles tiles of rows are FP32 and are
+// folded into FP64 accumulators (GB300's FP64 rate is low, so the fold is kept
+// rare), and all R x R work is FP64.  Every
+// reduction runs over fixed per-block partials in a fixed order, so results
+// are bitwise reproducible.
 #include <algorithm>
 #include <cmath>
 
@@ -22,90 +28,194 @@ dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out);
 
 namespace {
 
-constexpr int kRowThreads = 256;
-constexpr int kFold = 64;  // rows per FP32 partial before folding into FP64
+constexpr int kT = 256;          // threads of the row-pass and Gram kernels
+constexpr int kTile = 64;        // rows per staged tile
+constexpr int kFoldTiles = 8;    // tiles summed in FP32 before folding into FP64
 constexpr int kMaxBlocks = 152 * 4;
 constexpr int kMaxR = 128;
 
-unsigned row_blocks(int64_t rows, int rows_per_block = 64) {
-  int64_t b = (rows + rows_per_block - 1) / rows_per_block;
+unsigned row_blocks(int64_t rows) {
+  const int64_t b = (rows + 4 * kTile - 1) / (4 * kTile);
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, kMaxBlocks));
 }
 
-// ---------------------------------------------------------------------------
-// Cross Gram X^T Y of two rows x R matrices (X may equal Y), FP64 partial per
-// block: part[block][R*R].  Rows are staged in shared memory as float tiles.
-// ---------------------------------------------------------------------------
-template <typename TX, typename TY, int PER>
-__global__ void __launch_bounds__(kRowThreads) cross_gram_partials(const TX* __restrict__ X,
-                                                                  const TY* __restrict__ Y,
-                                                                  int64_t rows, int R,
-                                                                  double* __restrict__ part) {
-  extern __shared__ float tile[];  // [trows][R] X then [trows][R] Y
-  const int trows = min(kFold, 4096 / R);
-  float* tx = tile;
-  float* ty = tile + (size_t)trows * R;
-  const int RR = R * R;
-  constexpr int per = PER;  // entries per thread: ceil(R*R / threads)
-  double accd[PER];
-#pragma unroll
-  for (int q = 0; q < per; ++q) accd[q] = 0.0;
+// Rows [r0, r1) of the block's share of `rows` (contiguous chunks).
+__device__ __forceinline__ void block_rows(int64_t rows, int64_t& r0, int64_t& r1) {
   const int64_t chunk = (rows + gridDim.x - 1) / gridDim.x;
-  const int64_t r0 = (int64_t)blockIdx.x * chunk;
-  const int64_t r1 = min(rows, r0 + chunk);
-  for (int64_t t0 = r0; t0 < r1; t0 += trows) {
-    const int nt = (int)min((int64_t)trows, r1 - t0);
-    for (int e = threadIdx.x; e < nt * R; e += kRowThreads) {
-      tx[e] = ld_elem(X + t0 * R + e);
-      ty[e] = ld_elem(Y + t0 * R + e);
+  r0 = min(rows, (int64_t)blockIdx.x * chunk);
+  r1 = min(rows, r0 + chunk);
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic reduction of per-block partials: part is [nb][n];
+// out[e] = sum_b part[b][e] (+ part[b][e^T] when symmetrize, R x R entries).
+// Block x takes 32 entries (one per lane); its eight warps take blocks
+// b = w, w + 8, ... in order; the warp sums are added in warp order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kT) reduce_partials(const double* __restrict__ part, int nb, int n,
+                                                      int R, bool symmetrize,
+                                                      double* __restrict__ out) {
+  __shared__ double s[kT / 32][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  double acc = 0.0;
+  if (e < n) {
+    const int et = symmetrize ? (e % R) * R + e / R : e;
+    for (int b = warp; b < nb; b += kT / 32) {
+      acc += part[(size_t)b * n + e];
+      if (symmetrize) acc += part[(size_t)b * n + et];
+    }
+  }
+  s[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && e < n) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kT / 32; ++w) t += s[w][lane];
+    out[e] = t;
+  }
+}
+
+// Sum of the kT per-thread values v into thread 0 in a fixed order.
+__device__ __forceinline__ double block_sum(double v, double* s) {
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = kT / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double t = s[0];
+  __syncthreads();
+  return t;
+}
+
+// Four consecutive entries of a factor row in storage type T, widened.
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
+  const uint2 w = *reinterpret_cast<const uint2*>(p);
+  return make_float4(bf16_lo(w.x), bf16_hi(w.x), bf16_lo(w.y), bf16_hi(w.y));
+}
+
+// Stage rows [t0, t0 + nt) of an n x R matrix into `tile` (row stride ld
+// floats, columns R .. W-1 zero-filled).  Each thread owns a fixed (row offset,
+// column) slot, computed once: four columns at a time when R % 4 == 0 (16-byte
+// copies), one at a time otherwise.
+template <typename T>
+__device__ __forceinline__ void stage_tile(const T* __restrict__ M, int64_t t0, int nt, int R,
+                                           float* __restrict__ tile, int ld, int W) {
+  if ((R & 3) == 0) {
+    const int R4 = R >> 2, per = kT / R4;
+    const int i0 = threadIdx.x / R4, c = 4 * (threadIdx.x % R4);
+    if ((int)threadIdx.x < per * R4)
+      for (int i = i0; i < nt; i += per)
+        *reinterpret_cast<float4*>(tile + i * ld + c) = ld4(M + (t0 + i) * R + c);
+  } else {
+    const int per = kT / W;
+    const int i0 = threadIdx.x / W, c = threadIdx.x % W;
+    if ((int)threadIdx.x < per * W)
+      for (int i = i0; i < nt; i += per) tile[i * ld + c] = c < R ? ld_elem(M + (t0 + i) * R + c) : 0.f;
+  }
+}
+
+// Row stride of a staged tile read row-wise by row_times: a multiple of four
+// (16-byte aligned rows) shifted by four banks per row when R % 4 == 0.
+__host__ __device__ __forceinline__ int row_ld(int R) { return (R & 3) == 0 ? R + 4 : R + 1; }
+
+// ---------------------------------------------------------------------------
+// Gram X^T Y (X may be Y) of rows x R matrices: per-block FP64 partials
+// part[block][R*R].  Rows are staged as float tiles (columns padded to a
+// multiple of 4 with zeros); thread (blk, grp) owns the 4 x 4 block blk of the
+// result and the rows grp, grp + ngrp, ... of every tile.
+// ---------------------------------------------------------------------------
+template <typename TX, typename TY, bool SAME, int BPT>
+__global__ void __launch_bounds__(kT) gram_tiles(const TX* __restrict__ X, const TY* __restrict__ Y,
+                                                 int64_t rows, int R, double* __restrict__ part) {
+  extern __shared__ __align__(16) float sm[];
+  const int R4 = (R + 3) / 4, W = 4 * R4;
+  float* tx = sm;                                   // [kTile][W]
+  float* ty = SAME ? sm : sm + (size_t)kTile * W;   // [kTile][W]
+  const int nblk = R4 * R4;
+  const int ngrp = nblk <= kT ? kT / nblk : 1;
+  const int grp = nblk <= kT ? (int)threadIdx.x / nblk : 0;
+  const bool owner = nblk <= kT ? ((int)threadIdx.x < ngrp * nblk) : true;
+  double acc[BPT][16];
+  float a32[BPT][16];
+#pragma unroll
+  for (int b = 0; b < BPT; ++b)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) { acc[b][q] = 0.0; a32[b][q] = 0.f; }
+  int64_t r0, r1;
+  block_rows(rows, r0, r1);
+  int tiles = 0;
+  for (int64_t t0 = r0; t0 < r1; t0 += kTile) {
+    const int nt = (int)min((int64_t)kTile, r1 - t0);
+    stage_tile(X, t0, nt, R, tx, W, W);
+    if (!SAME) stage_tile(Y, t0, nt, R, ty, W, W);
+    __syncthreads();
+    if (owner) {
+#pragma unroll
+      for (int b = 0; b < BPT; ++b) {
+        const int blk = nblk <= kT ? (int)threadIdx.x % nblk : (int)threadIdx.x + b * kT;
+        if (blk < nblk) {
+          const int bi = blk / R4, bj = blk % R4;
+          for (int i = grp; i < nt; i += ngrp) {
+            const float4 xv = *reinterpret_cast<const float4*>(tx + i * W + 4 * bi);
+            const float4 yv = *reinterpret_cast<const float4*>(ty + i * W + 4 * bj);
+            const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int w = 0; w < 4; ++w) a32[b][u * 4 + w] = fmaf(xa[u], ya[w], a32[b][u * 4 + w]);
+          }
+        }
+      }
+    }
+    if (++tiles == kFoldTiles || t0 + kTile >= r1) {
+#pragma unroll
+      for (int b = 0; b < BPT; ++b)
+#pragma unroll
+        for (int q = 0; q < 16; ++q) { acc[b][q] += (double)a32[b][q]; a32[b][q] = 0.f; }
+      tiles = 0;
     }
     __syncthreads();
+  }
+  // Combine the row groups of each block in group order, write the partial.
+  double* red = reinterpret_cast<double*>(sm);  // [kT][16] (fits the tile space)
 #pragma unroll
-    for (int q = 0; q < per; ++q) {
-      const int ent = threadIdx.x + q * kRowThreads;
-      if (ent < RR) {
-        const int a = ent / R, b = ent % R;
-        float s = 0.f;
-        for (int i = 0; i < nt; ++i) s = fmaf(tx[i * R + a], ty[i * R + b], s);
-        accd[q] += (double)s;
+  for (int b = 0; b < BPT; ++b) {
+    const int blk = nblk <= kT ? (int)threadIdx.x % nblk : (int)threadIdx.x + b * kT;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) red[threadIdx.x * 16 + q] = acc[b][q];
+    __syncthreads();
+    if (owner && grp == 0 && blk < nblk) {
+      const int bi = blk / R4, bj = blk % R4;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        double t = 0.0;
+        for (int gg = 0; gg < ngrp; ++gg) t += red[(gg * nblk + (nblk <= kT ? blk : (int)threadIdx.x)) * 16 + q];
+        const int a = 4 * bi + q / 4, c = 4 * bj + q % 4;
+        if (a < R && c < R) part[(size_t)blockIdx.x * R * R + a * R + c] = t;
       }
     }
     __syncthreads();
   }
-#pragma unroll
-  for (int q = 0; q < per; ++q) {
-    const int ent = threadIdx.x + q * kRowThreads;
-    if (ent < RR) part[(size_t)blockIdx.x * RR + ent] = accd[q];
-  }
-}
-
-// out[e] = sum over blocks b (in order) of part[b][e]  (+ part^T if sym).
-__global__ void reduce_partials(const double* __restrict__ part, int nblocks, int n, int R,
-                                bool symmetrize, double* __restrict__ out) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * n + e];
-    if (symmetrize) {
-      const int a = e / R, c = e % R;
-      const int et = c * R + a;
-      for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * n + et];
-    }
-    out[e] = s;
-  }
 }
 
 // ---------------------------------------------------------------------------
-// Gamma = G_f * G_in + lambda_reg I and its inverse (or pseudo-inverse).
-// One CTA, FP64 in shared memory.  Cholesky fails when a pivot drops to
-// R * eps times its diagonal entry; then the cyclic Jacobi eigen-decomposition
-// gives the pseudo-inverse with eigenvalue cutoff R * eps * max |w|.
+// Gamma = G_f * G_in + lambda_reg I and its inverse (or pseudo-inverse), one
+// block, FP64.  Cholesky fails when a pivot drops to R * eps times its
+// diagonal entry; then the cyclic Jacobi eigen-decomposition (Golub & Van
+// Loan, Sec. 8.5) gives the pseudo-inverse with cutoff R * eps * max |w|.
+// The (2R^2 + R)-double workspace is shared memory when it fits, else global.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) gamma_inverse(const double* __restrict__ Gf,
                                                     const double* __restrict__ Gi, int R,
                                                     double lambda_reg, double* __restrict__ W,
                                                     float* __restrict__ W32,
                                                     int32_t* __restrict__ singular,
-                                                    double* __restrict__ work) {
+                                                    double* __restrict__ gwork, bool in_smem) {
+  extern __shared__ double swork[];
+  double* work = in_smem ? swork : gwork;
   double* A = work;               // [R][R] working copy / L
   double* B = work + R * R;       // [R][R] Linv or V
   double* d0 = work + 2 * R * R;  // [R] original diagonal / eigenvalues
@@ -114,9 +224,8 @@ __global__ void __launch_bounds__(256) gamma_inverse(const double* __restrict__ 
   const int RR = R * R;
   const double eps = 2.220446049250313e-16;
   for (int e = tid; e < RR; e += nt) {
-    const int a = e / R, b = e % R;
     double g = Gf[e] * Gi[e];
-    if (a == b) g += lambda_reg;
+    if (e / R == e % R) g += lambda_reg;
     A[e] = g;
   }
   if (tid == 0) failed = 0;
@@ -132,8 +241,8 @@ __global__ void __launch_bounds__(256) gamma_inverse(const double* __restrict__ 
     }
     __syncthreads();
     if (failed) break;
-    const double ljj = A[j * R + j];
-    for (int i = j + 1 + tid; i < R; i += nt) A[i * R + j] /= ljj;
+    const double rjj = 1.0 / A[j * R + j];
+    for (int i = j + 1 + tid; i < R; i += nt) A[i * R + j] *= rjj;
     __syncthreads();
     const int m = R - j - 1;
     for (int e = tid; e < m * m; e += nt) {
@@ -143,15 +252,18 @@ __global__ void __launch_bounds__(256) gamma_inverse(const double* __restrict__ 
     __syncthreads();
   }
   if (!failed) {
-    // Linv by forward substitution, one column per thread.
+    // Linv by forward substitution, one column per thread (reciprocal
+    // diagonal in d0).
+    for (int a = tid; a < R; a += nt) d0[a] = 1.0 / A[a * R + a];
+    __syncthreads();
     for (int c = tid; c < R; c += nt) {
       for (int i = 0; i < R; ++i) {
-        double s = (i == c) ? 1.0 : 0.0;
-        if (i >= c) {
-          for (int k = c; k < i; ++k) s -= A[i * R + k] * B[k * R + c];
-          B[i * R + c] = s / A[i * R + i];
-        } else {
+        if (i < c) {
           B[i * R + c] = 0.0;
+        } else {
+          double s = (i == c) ? 1.0 : 0.0;
+          for (int k = c; k < i; ++k) s -= A[i * R + k] * B[k * R + c];
+          B[i * R + c] = s * d0[i];
         }
       }
     }
@@ -166,7 +278,6 @@ __global__ void __launch_bounds__(256) gamma_inverse(const double* __restrict__ 
     }
     return;
   }
-  // Pseudo-inverse by cyclic Jacobi (Golub & Van Loan, Sec. 8.5).
   if (tid == 0) atomicOr(singular, 1);
   for (int e = tid; e < RR; e += nt) {
     const int a = e / R, b = e % R;
@@ -204,21 +315,21 @@ __global__ void __launch_bounds__(256) gamma_inverse(const double* __restrict__ 
           }
         }
         __syncthreads();
-        const double c = s_c, s = s_s;
-        if (s != 0.0) {
+        const double c = s_c, sn = s_s;
+        if (sn != 0.0) {
           for (int k = tid; k < R; k += nt) {  // columns p, q
             const double akp = A[k * R + p], akq = A[k * R + q];
-            A[k * R + p] = c * akp - s * akq;
-            A[k * R + q] = s * akp + c * akq;
+            A[k * R + p] = c * akp - sn * akq;
+            A[k * R + q] = sn * akp + c * akq;
           }
           __syncthreads();
-          for (int k = tid; k < R; k += nt) {  // rows p, q
+          for (int k = tid; k < R; k += nt) {  // rows p, q and V
             const double apk = A[p * R + k], aqk = A[q * R + k];
-            A[p * R + k] = c * apk - s * aqk;
-            A[q * R + k] = s * apk + c * aqk;
+            A[p * R + k] = c * apk - sn * aqk;
+            A[q * R + k] = sn * apk + c * aqk;
             const double vkp = B[k * R + p], vkq = B[k * R + q];
-            B[k * R + p] = c * vkp - s * vkq;
-            B[k * R + q] = s * vkp + c * vkq;
+            B[k * R + p] = c * vkp - sn * vkq;
+            B[k * R + q] = sn * vkp + c * vkq;
           }
         }
         __syncthreads();
@@ -240,153 +351,236 @@ __global__ void __launch_bounds__(256) gamma_inverse(const double* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Row-wise passes: one warp per row, lane owns columns lane, lane+32, ...
+// Row passes.  A block takes a contiguous chunk of rows in tiles of kTile; the
+// tile of the input rows is staged (row stride R + 1) and thread t computes
+// columns 4 (t % R4) .. +3 of rows t / R4, t / R4 + kT / R4, ... of the tile.
 // ---------------------------------------------------------------------------
 
-// Fhat[o,:] = N[o,:] W; column sums of squares of Fhat -> part[block][R].
-__global__ void __launch_bounds__(kRowThreads) als_colnorm_partials(const float* __restrict__ N,
-                                                                   const float* __restrict__ W32,
-                                                                   int64_t rows, int R,
-                                                                   double* __restrict__ part) {
-  extern __shared__ float sW[];  // [R][R]
-  __shared__ double sacc[kRowThreads / 32][kMaxR];
-  for (int e = threadIdx.x; e < R * R; e += kRowThreads) sW[e] = W32[e];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float accf[4] = {0.f, 0.f, 0.f, 0.f};
-  double accd[4] = {0.0, 0.0, 0.0, 0.0};
-  int since = 0;
-  const int64_t wstride = (int64_t)gridDim.x * (kRowThreads / 32);
-  for (int64_t o = (int64_t)blockIdx.x * (kRowThreads / 32) + warp; o < rows; o += wstride) {
-    float nrow[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) nrow[q] = (lane + 32 * q < R) ? N[o * R + lane + 32 * q] : 0.f;
-    float f[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int k = 0; k < R; ++k) {
-      const float nk = __shfl_sync(kFull, nrow[k >> 5], k & 31);
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (lane + 32 * q < R) f[q] = fmaf(nk, sW[k * R + lane + 32 * q], f[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) accf[q] = fmaf(f[q], f[q], accf[q]);
-    if (++since == kFold) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) { accd[q] += accf[q]; accf[q] = 0.f; }
-      since = 0;
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    accd[q] += accf[q];
-    if (lane + 32 * q < R) sacc[warp][lane + 32 * q] = accd[q];
-  }
-  __syncthreads();
-  for (int col = threadIdx.x; col < R; col += kRowThreads) {
-    double s = 0.0;
-    for (int w = 0; w < kRowThreads / 32; ++w) s += sacc[w][col];
-    part[(size_t)blockIdx.x * R + col] = s;
+// Row r of a staged tile times the R x R matrix S (in shared memory): four
+// consecutive output columns starting at 4 * cg.
+__device__ __forceinline__ void row_times(const float* __restrict__ trow, const float* __restrict__ S,
+                                          int R, int W, int cg, float (&o)[4]) {
+  o[0] = o[1] = o[2] = o[3] = 0.f;
+  for (int k = 0; k < R; ++k) {
+    const float a = trow[k];
+    const float4 w = *reinterpret_cast<const float4*>(S + k * W + 4 * cg);
+    o[0] = fmaf(a, w.x, o[0]);
+    o[1] = fmaf(a, w.y, o[1]);
+    o[2] = fmaf(a, w.z, o[2]);
+    o[3] = fmaf(a, w.w, o[3]);
   }
 }
 
-// lambda[r] = sqrt(sum of partials); inv[r] = 1/lambda (0 -> leave column).
-__global__ void finish_lambda(const double* __restrict__ part, int nblocks, int R,
-                              double* __restrict__ lambda, float* __restrict__ inv) {
-  for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * R + r];
-    const double l = sqrt(s);
+// Stage an R x R FP32 matrix with rows padded to W = 4 * R4 columns.
+__device__ __forceinline__ void stage_rr(const float* __restrict__ M, int R, int W, float* S) {
+  for (int e = threadIdx.x; e < R * W; e += kT) {
+    const int k = e / W, c = e % W;
+    S[e] = c < R ? M[k * R + c] : 0.f;
+  }
+}
+
+// ALS pass A: Fh = N W (W = Gamma^{-1}) and per-block column sums of squares
+// of Fh, colsq[block][R].
+__global__ void __launch_bounds__(kT) als_solve_rows(const float* __restrict__ N,
+                                                     const float* __restrict__ W32, int64_t rows,
+                                                     int R, float* __restrict__ Fh,
+                                                     double* __restrict__ colsq) {
+  extern __shared__ __align__(16) float sm[];
+  const int R4 = (R + 3) / 4, W = 4 * R4;
+  float* S = sm;                        // [R][W]
+  float* tile = sm + (size_t)R * W;     // [kTile][row_ld(R)]
+  const int ld = row_ld(R);
+  __shared__ double red[kT];
+  stage_rr(W32, R, W, S);
+  const int cg = threadIdx.x % R4, rsub = threadIdx.x / R4, rstep = kT / R4;
+  const bool active = rsub < rstep;
+  double sq[4] = {0.0, 0.0, 0.0, 0.0};
+  int64_t r0, r1;
+  block_rows(rows, r0, r1);
+  for (int64_t t0 = r0; t0 < r1; t0 += kTile) {
+    const int nt = (int)min((int64_t)kTile, r1 - t0);
+    __syncthreads();
+    stage_tile(N, t0, nt, R, tile, ld, R);
+    __syncthreads();
+    float s32[4] = {0.f, 0.f, 0.f, 0.f};
+    if (active) {
+      for (int i = rsub; i < nt; i += rstep) {
+        float o[4];
+        row_times(tile + i * ld, S, R, W, cg, o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int col = 4 * cg + q;
+          if (col < R) {
+            Fh[(t0 + i) * R + col] = o[q];
+            s32[q] = fmaf(o[q], o[q], s32[q]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sq[q] += (double)s32[q];
+  }
+  // Column c is owned by the threads with cg = c / 4: add them in thread order.
+  for (int c = 0; c < R; ++c) {
+    const double v = (active && cg == c / 4) ? sq[c % 4] : 0.0;
+    const double t = block_sum(v, red);
+    if (threadIdx.x == 0) colsq[(size_t)blockIdx.x * R + c] = t;
+  }
+}
+
+// lambda[r] = sqrt(sum_b colsq[b][r]); inv[r] = 1/lambda (1 where lambda = 0).
+// One block per column.
+__global__ void __launch_bounds__(kT) finish_lambda(const double* __restrict__ colsq, int nb, int R,
+                                                    double* __restrict__ lambda,
+                                                    float* __restrict__ inv) {
+  __shared__ double red[kT];
+  const int r = blockIdx.x;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kT) v += colsq[(size_t)b * R + r];
+  const double t = block_sum(v, red);
+  if (threadIdx.x == 0) {
+    const double l = sqrt(t);
     lambda[r] = l;
     inv[r] = (l > 0.0) ? (float)(1.0 / l) : 1.0f;
   }
 }
 
-// F[o,:] = (N[o,:] W) / lambda, stored in T.  With ipart != null also
-// accumulates sum_o F_stored[o,r] * N[o,r] (-> <X, Xhat> after a mode-3 update).
-template <typename T>
-__global__ void __launch_bounds__(kRowThreads) als_normalize(const float* __restrict__ N,
-                                                            const float* __restrict__ W32,
-                                                            const float* __restrict__ inv,
-                                                            int64_t rows, int R, T* __restrict__ F,
-                                                            double* __restrict__ ipart) {
-  extern __shared__ float sW[];  // [R][R]
-  __shared__ double sacc[kRowThreads / 32][kMaxR];
-  for (int e = threadIdx.x; e < R * R; e += kRowThreads) sW[e] = W32[e];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float sc[4];
+// ALS pass B: F = Fh / lambda stored in T; Gram partials of the stored values
+// gpart[block][R*R]; with N != null also the scalar partial
+// sum_{o,r} lambda_r F_stored[o,r] N[o,r] (= <X, Xhat> after the mode-3 update).
+template <typename T, int BPT>
+__global__ void __launch_bounds__(kT) als_store_rows(const float* __restrict__ Fh,
+                                                     const float* __restrict__ inv,
+                                                     const double* __restrict__ lambda,
+                                                     int64_t rows, int R, T* __restrict__ F,
+                                                     double* __restrict__ gpart,
+                                                     const float* __restrict__ N,
+                                                     double* __restrict__ ipart) {
+  extern __shared__ __align__(16) float sm[];
+  const int R4 = (R + 3) / 4, W = 4 * R4;
+  float* tile = sm;  // [kTile][W] stored values, zero-padded
+  __shared__ double red[kT];
+  const int nblk = R4 * R4;
+  const int ngrp = nblk <= kT ? kT / nblk : 1;
+  const int grp = nblk <= kT ? (int)threadIdx.x / nblk : 0;
+  const bool owner = nblk <= kT ? ((int)threadIdx.x < ngrp * nblk) : true;
+  double acc[BPT][16];  // BPT = 1 when R <= 64, else 4 blocks per thread
+  float a32[BPT][16];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) sc[q] = (lane + 32 * q < R) ? inv[lane + 32 * q] : 0.f;
-  float accf[4] = {0.f, 0.f, 0.f, 0.f};
-  double accd[4] = {0.0, 0.0, 0.0, 0.0};
-  int since = 0;
-  const int64_t wstride = (int64_t)gridDim.x * (kRowThreads / 32);
-  for (int64_t o = (int64_t)blockIdx.x * (kRowThreads / 32) + warp; o < rows; o += wstride) {
-    float nrow[4];
+  for (int b = 0; b < BPT; ++b)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) nrow[q] = (lane + 32 * q < R) ? N[o * R + lane + 32 * q] : 0.f;
-    float f[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int k = 0; k < R; ++k) {
-      const float nk = __shfl_sync(kFull, nrow[k >> 5], k & 31);
+    for (int q = 0; q < 16; ++q) { acc[b][q] = 0.0; a32[b][q] = 0.f; }
+  int tiles = 0;
+  double ip = 0.0;
+  int64_t r0, r1;
+  block_rows(rows, r0, r1);
+  for (int64_t t0 = r0; t0 < r1; t0 += kTile) {
+    const int nt = (int)min((int64_t)kTile, r1 - t0);
+    __syncthreads();
+    float ip32 = 0.f;
+    {
+      // thread slot: columns c .. c + CW - 1 of rows i0, i0 + per, ...
+      const int CW = (R & 3) == 0 ? 4 : 1;
+      const int ncol = (R & 3) == 0 ? (R >> 2) : W;
+      const int per = kT / ncol;
+      const int i0 = threadIdx.x / ncol, c = CW * (threadIdx.x % ncol);
+      if ((int)threadIdx.x < per * ncol) {
+        float sc[4], lm[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (lane + 32 * q < R) f[q] = fmaf(nk, sW[k * R + lane + 32 * q], f[q]);
-    }
+        for (int q = 0; q < 4; ++q) {
+          sc[q] = (q < CW && c + q < R) ? inv[c + q] : 0.f;
+          lm[q] = (N && q < CW && c + q < R) ? (float)lambda[c + q] : 0.f;
+        }
+        for (int i = i0; i < kTile; i += per) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int col = lane + 32 * q;
-      if (col < R) {
-        const float val = f[q] * sc[q];
-        st_elem(F + o * R + col, val);
-        if (ipart) accf[q] = fmaf(rt_elem(F, val), nrow[q], accf[q]);
+          for (int q = 0; q < 4; ++q) {
+            if (q >= CW) break;
+            float v = 0.f;
+            if (i < nt && c + q < R) {
+              const int64_t g = (t0 + i) * R + c + q;
+              const float x = Fh[g] * sc[q];
+              st_elem(F + g, x);
+              v = rt_elem(F, x);
+              if (N) ip32 = fmaf(lm[q] * v, N[g], ip32);
+            }
+            tile[i * W + c + q] = v;
+          }
+        }
       }
     }
-    if (ipart && ++since == kFold) {
+    ip += (double)ip32;
+    __syncthreads();
+    if (owner) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) { accd[q] += accf[q]; accf[q] = 0.f; }
-      since = 0;
+      for (int b = 0; b < BPT; ++b) {
+        const int blk = nblk <= kT ? (int)threadIdx.x % nblk : (int)threadIdx.x + b * kT;
+        if (blk >= nblk) continue;
+        const int bi = blk / R4, bj = blk % R4;
+        for (int i = grp; i < nt; i += ngrp) {
+          const float4 xv = *reinterpret_cast<const float4*>(tile + i * W + 4 * bi);
+          const float4 yv = *reinterpret_cast<const float4*>(tile + i * W + 4 * bj);
+          const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) a32[b][u * 4 + w] = fmaf(xa[u], ya[w], a32[b][u * 4 + w]);
+        }
+      }
+    }
+    if (++tiles == kFoldTiles || t0 + kTile >= r1) {
+#pragma unroll
+      for (int b = 0; b < BPT; ++b)
+#pragma unroll
+        for (int q = 0; q < 16; ++q) { acc[b][q] += (double)a32[b][q]; a32[b][q] = 0.f; }
+      tiles = 0;
     }
   }
-  if (!ipart) return;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    accd[q] += accf[q];
-    if (lane + 32 * q < R) sacc[warp][lane + 32 * q] = accd[q];
+  if (N) {
+    const double t = block_sum(ip, red);
+    if (threadIdx.x == 0) ipart[blockIdx.x] = t;
   }
   __syncthreads();
-  for (int col = threadIdx.x; col < R; col += kRowThreads) {
-    double s = 0.0;
-    for (int w = 0; w < kRowThreads / 32; ++w) s += sacc[w][col];
-    ipart[(size_t)blockIdx.x * R + col] = s;
+  double* rsm = reinterpret_cast<double*>(sm);  // [kT][16] over the tile space
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    const int blk = nblk <= kT ? (int)threadIdx.x % nblk : (int)threadIdx.x + b * kT;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) rsm[threadIdx.x * 16 + q] = acc[b][q];
+    __syncthreads();
+    if (owner && grp == 0 && blk < nblk) {
+      const int bi = blk / R4, bj = blk % R4;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        double t = 0.0;
+        for (int gg = 0; gg < ngrp; ++gg)
+          t += rsm[(gg * nblk + (nblk <= kT ? blk : (int)threadIdx.x)) * 16 + q];
+        const int a = 4 * bi + q / 4, c = 4 * bj + q % 4;
+        if (a < R && c < R) gpart[(size_t)blockIdx.x * R * R + a * R + c] = t;
+      }
+    }
+    __syncthreads();
   }
 }
 
-// Fit from scalars and Grams (one thread block):
-//   <X,Xhat> = sum_r lambda_r * ip[r];  ||Xhat||^2 = lambda^T (GA*GB*GC) lambda.
-__global__ void fit_from_parts(const double* __restrict__ ipart, int nblocks, int R,
-                               const double* __restrict__ lambda, const double* __restrict__ GA,
-                               const double* __restrict__ GB, const double* __restrict__ GC,
-                               double* __restrict__ scal) {
-  __shared__ double s_ip[kMaxR];
-  __shared__ double s_red[256];
-  const int tid = threadIdx.x;
-  for (int r = tid; r < R; r += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += ipart[(size_t)b * R + r];
-    s_ip[r] = s;
-  }
+// Fit from scalars and Grams (one block):
+//   <X,Xhat> = sum of ipart;  ||Xhat||^2 = lambda^T (GA*GB*GC) lambda.
+__global__ void __launch_bounds__(kT) fit_from_parts(const double* __restrict__ ipart, int nb, int R,
+                                                     const double* __restrict__ lambda,
+                                                     const double* __restrict__ GA,
+                                                     const double* __restrict__ GB,
+                                                     const double* __restrict__ GC,
+                                                     double* __restrict__ scal) {
+  __shared__ double red[kT];
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kT) v += ipart[b];
+  const double ip = block_sum(v, red);
   double m = 0.0;
-  for (int e = tid; e < R * R; e += blockDim.x) {
+  for (int e = threadIdx.x; e < R * R; e += kT) {
     const int a = e / R, b = e % R;
     m += lambda[a] * lambda[b] * GA[e] * GB[e] * GC[e];
   }
-  s_red[tid] = m;
-  __syncthreads();
-  if (tid == 0) {
-    double nm2 = 0.0;
-    for (int t = 0; t < (int)blockDim.x; ++t) nm2 += s_red[t];
-    double ip = 0.0;
-    for (int r = 0; r < R; ++r) ip += lambda[r] * s_ip[r];
+  const double nm2 = block_sum(m, red);
+  if (threadIdx.x == 0) {
     const double nx2 = scal[kNormX2];
     double res2 = nx2 - 2.0 * ip + nm2;
     if (res2 < 0.0) res2 = 0.0;
@@ -396,71 +590,86 @@ __global__ void fit_from_parts(const double* __restrict__ ipart, int nblocks, in
   }
 }
 
+// <N, lambda-scaled F> partials for a fit without an ALS sweep.
+template <typename T>
+__global__ void __launch_bounds__(kT) rows_inner(const float* __restrict__ N, const T* __restrict__ F,
+                                                 const double* __restrict__ lambda, int64_t rows,
+                                                 int R, double* __restrict__ ipart) {
+  __shared__ double red[kT];
+  int64_t r0, r1;
+  block_rows(rows, r0, r1);
+  double acc = 0.0;
+  float a32 = 0.f;
+  int since = 0;
+  for (int64_t g = r0 * R + threadIdx.x; g < r1 * R; g += kT) {
+    a32 = fmaf((float)lambda[g % R] * ld_elem(F + g), N[g], a32);
+    if (++since == kTile) {
+      acc += a32;
+      a32 = 0.f;
+      since = 0;
+    }
+  }
+  acc += a32;
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) ipart[blockIdx.x] = t;
+}
+
 // ---------------------------------------------------------------------------
 // GD.
 // ---------------------------------------------------------------------------
 
-// grad[o,:] = -N[o,:] + F[o,:] Gamma (Gamma already holds + lambda_reg I).
-// Scalar partials per block (FP64): [0] ||grad||^2, [1] sum grad*N, [2] sum F*N.
+// grad = -N + F Gamma (Gamma already holds + lambda_reg I); scalar partials
+// per block: spart[block][3] = ||grad||^2, sum grad*N, sum F*N.
 template <typename T>
-__global__ void __launch_bounds__(kRowThreads) gd_gradient_rows(const float* __restrict__ N,
-                                                               const T* __restrict__ F,
-                                                               const float* __restrict__ Gam32,
-                                                               int64_t rows, int R,
-                                                               float* __restrict__ grad,
-                                                               double* __restrict__ spart) {
-  extern __shared__ float sG[];  // [R][R]
-  __shared__ double sred[3][kRowThreads / 32];
-  for (int e = threadIdx.x; e < R * R; e += kRowThreads) sG[e] = Gam32[e];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float af[3] = {0.f, 0.f, 0.f};
+__global__ void __launch_bounds__(kT) gd_gradient_rows(const float* __restrict__ N,
+                                                       const T* __restrict__ F,
+                                                       const float* __restrict__ Gam32,
+                                                       int64_t rows, int R,
+                                                       float* __restrict__ grad,
+                                                       double* __restrict__ spart) {
+  extern __shared__ __align__(16) float sm[];
+  const int R4 = (R + 3) / 4, W = 4 * R4;
+  float* S = sm;                     // [R][W]
+  float* tile = sm + (size_t)R * W;  // [kTile][row_ld(R)] rows of F
+  const int ld = row_ld(R);
+  __shared__ double red[kT];
+  stage_rr(Gam32, R, W, S);
+  const int cg = threadIdx.x % R4, rsub = threadIdx.x / R4, rstep = kT / R4;
+  const bool active = rsub < rstep;
   double ad[3] = {0.0, 0.0, 0.0};
-  int since = 0;
-  const int64_t wstride = (int64_t)gridDim.x * (kRowThreads / 32);
-  for (int64_t o = (int64_t)blockIdx.x * (kRowThreads / 32) + warp; o < rows; o += wstride) {
-    float frow[4], nrow[4];
+  int64_t r0, r1;
+  block_rows(rows, r0, r1);
+  for (int64_t t0 = r0; t0 < r1; t0 += kTile) {
+    const int nt = (int)min((int64_t)kTile, r1 - t0);
+    __syncthreads();
+    stage_tile(F, t0, nt, R, tile, ld, R);
+    __syncthreads();
+    float af[3] = {0.f, 0.f, 0.f};
+    if (active) {
+      for (int i = rsub; i < nt; i += rstep) {
+        float o[4];
+        row_times(tile + i * ld, S, R, W, cg, o);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int col = lane + 32 * q;
-      frow[q] = (col < R) ? ld_elem(F + o * R + col) : 0.f;
-      nrow[q] = (col < R) ? N[o * R + col] : 0.f;
-    }
-    float g[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int k = 0; k < R; ++k) {
-      const float fk = __shfl_sync(kFull, frow[k >> 5], k & 31);
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (lane + 32 * q < R) g[q] = fmaf(fk, sG[k * R + lane + 32 * q], g[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int col = lane + 32 * q;
-      if (col < R) {
-        const float gv = g[q] - nrow[q];
-        grad[o * R + col] = gv;
-        af[0] = fmaf(gv, gv, af[0]);
-        af[1] = fmaf(gv, nrow[q], af[1]);
-        af[2] = fmaf(frow[q], nrow[q], af[2]);
+        for (int q = 0; q < 4; ++q) {
+          const int col = 4 * cg + q;
+          if (col < R) {
+            const int64_t g = (t0 + i) * R + col;
+            const float nv = N[g];
+            const float gv = o[q] - nv;
+            grad[g] = gv;
+            af[0] = fmaf(gv, gv, af[0]);
+            af[1] = fmaf(gv, nv, af[1]);
+            af[2] = fmaf(tile[i * ld + col], nv, af[2]);
+          }
+        }
       }
     }
-    if (++since == kFold) {
 #pragma unroll
-      for (int t = 0; t < 3; ++t) { ad[t] += af[t]; af[t] = 0.f; }
-      since = 0;
-    }
+    for (int t = 0; t < 3; ++t) ad[t] += (double)af[t];
   }
-#pragma unroll
   for (int t = 0; t < 3; ++t) {
-    ad[t] += af[t];
-    ad[t] = warp_sum(ad[t]);
-    if (lane == 0) sred[t][warp] = ad[t];
-  }
-  __syncthreads();
-  if (threadIdx.x < 3) {
-    double s = 0.0;
-    for (int w = 0; w < kRowThreads / 32; ++w) s += sred[threadIdx.x][w];
-    spart[(size_t)blockIdx.x * 3 + threadIdx.x] = s;
+    const double v = block_sum(ad[t], red);
+    if (threadIdx.x == 0) spart[(size_t)blockIdx.x * 3 + t] = v;
   }
 }
 
@@ -476,14 +685,21 @@ __global__ void hadamard_gamma(const double* __restrict__ Gf, const double* __re
   }
 }
 
-// Sum scalar partials [nblocks][k] in block order into scal[dst + i].
-__global__ void reduce_scalars(const double* __restrict__ part, int nblocks, int k,
-                               double* __restrict__ scal, int dst0, int dst1, int dst2) {
-  if (threadIdx.x < k) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * k + threadIdx.x];
-    const int dst = threadIdx.x == 0 ? dst0 : (threadIdx.x == 1 ? dst1 : dst2);
-    if (dst >= 0) scal[dst] = (dst == kG2) ? scal[dst] + s : s;
+// Sum the [nb][3] scalar partials of one mode (fixed order) and record them:
+// ||grad||^2 accumulates into scal[kG2]; <grad, N> -> dst1; <F, N> -> dst2.
+__global__ void __launch_bounds__(kT) gd_scalars(const double* __restrict__ spart, int nb,
+                                                 double* __restrict__ scal, int dst1, int dst2) {
+  __shared__ double red[kT];
+  double v[3];
+  for (int t = 0; t < 3; ++t) {
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kT) a += spart[(size_t)b * 3 + t];
+    v[t] = block_sum(a, red);
+  }
+  if (threadIdx.x == 0) {
+    scal[kG2] += v[0];
+    scal[dst1] = v[1];
+    if (dst2 >= 0) scal[dst2] = v[2];
   }
 }
 
@@ -588,34 +804,42 @@ __global__ void gd_update(T* __restrict__ F, const float* __restrict__ grad, int
 
 namespace {
 
-// Kernels that stage an R x R matrix in shared memory need the opt-in limit
-// above 48 KB once R > 110.
+// Kernels that stage R x R matrices or row tiles need the opt-in shared memory
+// limit for large R.
 template <typename K>
 void allow_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename TX, typename TY>
+size_t tile_bytes(int R, int copies) {
+  const int W = 4 * ((R + 3) / 4);
+  return std::max(sizeof(float) * (size_t)kTile * W * copies, sizeof(double) * kT * 16);
+}
+
+size_t solve_bytes(int R) {
+  const int W = 4 * ((R + 3) / 4);
+  return sizeof(float) * ((size_t)R * W + (size_t)kTile * row_ld(R));
+}
+
+template <typename TX, typename TY, bool SAME>
 dfacto_status cross_gram(dfacto_t* h, const TX* X, const TY* Y, int64_t rows, double* out,
                          bool symmetrize) {
   const int R = h->R;
-  const unsigned nb = row_blocks(rows, 256);
-  const int trows = std::min(kFold, 4096 / R);
-  const size_t smem = sizeof(float) * 2 * (size_t)trows * R;
+  const int R4 = (R + 3) / 4;
+  const unsigned nb = row_blocks(rows);
   if ((int64_t)nb * R * R > h->partials_cap) return fail(h, DFACTO_EINTERNAL, "partials too small");
-  const int per = (R * R + kRowThreads - 1) / kRowThreads;
-  if (per <= 1) {
-    cross_gram_partials<TX, TY, 1><<<nb, kRowThreads, smem, h->stream>>>(X, Y, rows, R, h->partials);
-  } else if (per <= 4) {
-    cross_gram_partials<TX, TY, 4><<<nb, kRowThreads, smem, h->stream>>>(X, Y, rows, R, h->partials);
-  } else if (per <= 16) {
-    cross_gram_partials<TX, TY, 16><<<nb, kRowThreads, smem, h->stream>>>(X, Y, rows, R, h->partials);
+  const size_t smem = tile_bytes(R, SAME ? 1 : 2);
+  if (R4 * R4 <= kT) {
+    allow_smem(gram_tiles<TX, TY, SAME, 1>, smem);
+    gram_tiles<TX, TY, SAME, 1><<<nb, kT, smem, h->stream>>>(X, Y, rows, R, h->partials);
   } else {
-    cross_gram_partials<TX, TY, 64><<<nb, kRowThreads, smem, h->stream>>>(X, Y, rows, R, h->partials);
+    allow_smem(gram_tiles<TX, TY, SAME, 4>, smem);
+    gram_tiles<TX, TY, SAME, 4><<<nb, kT, smem, h->stream>>>(X, Y, rows, R, h->partials);
   }
   DF_COUNT();
-  reduce_partials<<<(R * R + 255) / 256, 256, 0, h->stream>>>(h->partials, (int)nb, R * R, R,
-                                                               symmetrize, out); DF_COUNT();
+  reduce_partials<<<(R * R + 31) / 32, kT, 0, h->stream>>>(h->partials, (int)nb, R * R, R, symmetrize,
+                                                           out);
+  DF_COUNT();
   DF_CUDA(h, cudaGetLastError());
   return DFACTO_OK;
 }
@@ -623,7 +847,19 @@ dfacto_status cross_gram(dfacto_t* h, const TX* X, const TY* Y, int64_t rows, do
 template <typename T>
 dfacto_status gram_T(dfacto_t* h, int m) {
   const T* F = static_cast<const T*>(h->F[m]);
-  return cross_gram<T, T>(h, F, F, h->dims[m], h->gram[m], false);
+  return cross_gram<T, T, true>(h, F, F, h->dims[m], h->gram[m], false);
+}
+
+dfacto_status launch_gamma_inverse(dfacto_t* h, const double* Gf, const double* Gi) {
+  const int R = h->R;
+  const size_t need = sizeof(double) * (2 * (size_t)R * R + R);
+  const bool in_smem = need <= 48 * 1024;
+  gamma_inverse<<<1, 256, in_smem ? need : 0, h->stream>>>(Gf, Gi, R, h->lambda_reg, h->W, h->W32,
+                                                           h->flags + kFlagSingular, h->rr_work,
+                                                           in_smem);
+  DF_COUNT();
+  DF_CUDA(h, cudaGetLastError());
+  return DFACTO_OK;
 }
 
 }  // namespace
@@ -640,34 +876,41 @@ template <typename T>
 dfacto_status als_mode_T(dfacto_t* h, int mode) {
   const ModeCSR& M = h->m[mode];
   const int R = h->R;
+  const int R4 = (R + 3) / 4;
   cudaStream_t s = h->stream;
   dfacto_status st;
   for (int m : {M.f, M.in})
     if (!h->gram_valid[m] && (st = gram_of_factor(h, m)) != DFACTO_OK) return st;
-  gamma_inverse<<<1, 256, 0, s>>>(h->gram[M.f], h->gram[M.in], R, h->lambda_reg, h->W, h->W32,
-                                  h->flags + kFlagSingular, h->rr_work); DF_COUNT();
-  DF_CUDA(h, cudaGetLastError());
+  if ((st = launch_gamma_inverse(h, h->gram[M.f], h->gram[M.in])) != DFACTO_OK) return st;
   if ((st = mttkrp_launch(h, mode, h->N)) != DFACTO_OK) return st;
   const int64_t rows = M.dim_o;
   const unsigned nb = row_blocks(rows);
-  const size_t smem = sizeof(float) * R * R;
-  allow_smem(als_colnorm_partials, smem);
-  allow_smem(als_normalize<T>, smem);
-  als_colnorm_partials<<<nb, kRowThreads, smem, s>>>(h->N, h->W32, rows, R, h->partials); DF_COUNT();
-  finish_lambda<<<1, 128, 0, s>>>(h->partials, (int)nb, R, h->lambda, h->inv_lambda); DF_COUNT();
+  const size_t smem_a = solve_bytes(R);
+  allow_smem(als_solve_rows, smem_a);
+  als_solve_rows<<<nb, kT, smem_a, s>>>(h->N, h->W32, rows, R, h->Fh, h->partials);
+  DF_COUNT();
+  finish_lambda<<<R, kT, 0, s>>>(h->partials, (int)nb, R, h->lambda, h->inv_lambda);
+  DF_COUNT();
   const bool last = (mode == 2);
-  als_normalize<T><<<nb, kRowThreads, smem, s>>>(h->N, h->W32, h->inv_lambda, rows, R,
-                                                 static_cast<T*>(h->F[mode]),
-                                                 last ? h->partials : nullptr); DF_COUNT();
-  DF_CUDA(h, cudaGetLastError());
-  h->gram_valid[mode] = false;
-  if (last) {
-    // keep the <X,Xhat> partials: move them out of the way of the Gram below
-    DF_CUDA(h, cudaMemcpyAsync(h->ipart, h->partials, sizeof(double) * nb * R,
-                               cudaMemcpyDeviceToDevice, s));
-    h->ipart_blocks = (int)nb;
+  const size_t smem_b = tile_bytes(R, 1);
+  T* F = static_cast<T*>(h->F[mode]);
+  if (R4 * R4 <= kT) {
+    allow_smem(als_store_rows<T, 1>, smem_b);
+    als_store_rows<T, 1><<<nb, kT, smem_b, s>>>(h->Fh, h->inv_lambda, h->lambda, rows, R, F,
+                                                h->partials, last ? h->N : nullptr, h->ipart);
+  } else {
+    allow_smem(als_store_rows<T, 4>, smem_b);
+    als_store_rows<T, 4><<<nb, kT, smem_b, s>>>(h->Fh, h->inv_lambda, h->lambda, rows, R, F,
+                                                h->partials, last ? h->N : nullptr, h->ipart);
   }
-  return gram_of_factor(h, mode);
+  DF_COUNT();
+  reduce_partials<<<(R * R + 31) / 32, kT, 0, s>>>(h->partials, (int)nb, R * R, R, false,
+                                                   h->gram[mode]);
+  DF_COUNT();
+  DF_CUDA(h, cudaGetLastError());
+  h->gram_valid[mode] = true;
+  if (last) h->ipart_blocks = (int)nb;
+  return DFACTO_OK;
 }
 
 }  // namespace
@@ -677,8 +920,9 @@ dfacto_status als_mode(dfacto_t* h, int mode) {
 }
 
 dfacto_status als_fit(dfacto_t* h) {
-  fit_from_parts<<<1, 256, 0, h->stream>>>(h->ipart, h->ipart_blocks, h->R, h->lambda, h->gram[0],
-                                           h->gram[1], h->gram[2], h->scal); DF_COUNT();
+  fit_from_parts<<<1, kT, 0, h->stream>>>(h->ipart, h->ipart_blocks, h->R, h->lambda, h->gram[0],
+                                          h->gram[1], h->gram[2], h->scal);
+  DF_COUNT();
   DF_CUDA(h, cudaGetLastError());
   return DFACTO_OK;
 }
@@ -687,42 +931,6 @@ dfacto_status als_fit(dfacto_t* h) {
 // MTTKRP, sum_k sum_r lambda_r C[k,r] M3[k,r].
 namespace {
 template <typename T>
-__global__ void __launch_bounds__(kRowThreads) rows_dot_partials(const float* __restrict__ N,
-                                                                const T* __restrict__ F,
-                                                                int64_t rows, int R,
-                                                                double* __restrict__ part) {
-  __shared__ double sacc[kRowThreads / 32][kMaxR];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float accf[4] = {0.f, 0.f, 0.f, 0.f};
-  double accd[4] = {0.0, 0.0, 0.0, 0.0};
-  int since = 0;
-  const int64_t wstride = (int64_t)gridDim.x * (kRowThreads / 32);
-  for (int64_t o = (int64_t)blockIdx.x * (kRowThreads / 32) + warp; o < rows; o += wstride) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int col = lane + 32 * q;
-      if (col < R) accf[q] = fmaf(ld_elem(F + o * R + col), N[o * R + col], accf[q]);
-    }
-    if (++since == kFold) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) { accd[q] += accf[q]; accf[q] = 0.f; }
-      since = 0;
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    accd[q] += accf[q];
-    if (lane + 32 * q < R) sacc[warp][lane + 32 * q] = accd[q];
-  }
-  __syncthreads();
-  for (int col = threadIdx.x; col < R; col += kRowThreads) {
-    double s = 0.0;
-    for (int w = 0; w < kRowThreads / 32; ++w) s += sacc[w][col];
-    part[(size_t)blockIdx.x * R + col] = s;
-  }
-}
-
-template <typename T>
 dfacto_status fit_direct_T(dfacto_t* h) {
   dfacto_status st;
   for (int m = 0; m < 3; ++m)
@@ -730,8 +938,9 @@ dfacto_status fit_direct_T(dfacto_t* h) {
   if ((st = mttkrp_launch(h, 2, h->N)) != DFACTO_OK) return st;
   const int64_t rows = h->dims[2];
   const unsigned nb = row_blocks(rows);
-  rows_dot_partials<T><<<nb, kRowThreads, 0, h->stream>>>(h->N, static_cast<const T*>(h->F[2]),
-                                                          rows, h->R, h->ipart); DF_COUNT();
+  rows_inner<T><<<nb, kT, 0, h->stream>>>(h->N, static_cast<const T*>(h->F[2]), h->lambda, rows,
+                                          h->R, h->ipart);
+  DF_COUNT();
   DF_CUDA(h, cudaGetLastError());
   h->ipart_blocks = (int)nb;
   return als_fit(h);
@@ -760,34 +969,40 @@ dfacto_status gd_step_T(dfacto_t* h) {
   DF_CUDA(h, cudaMemsetAsync(h->scal + kG2, 0, sizeof(double), s));
   for (int mode = 0; mode < 3; ++mode) {
     const ModeCSR& M = h->m[mode];
-    hadamard_gamma<<<1, 256, 0, s>>>(h->gram[M.f], h->gram[M.in], R, h->lambda_reg, h->W, h->W32); DF_COUNT();
+    hadamard_gamma<<<1, 256, 0, s>>>(h->gram[M.f], h->gram[M.in], R, h->lambda_reg, h->W, h->W32);
+    DF_COUNT();
     if ((st = mttkrp_launch(h, mode, h->N)) != DFACTO_OK) return st;
     const int64_t rows = M.dim_o;
     const unsigned nb = row_blocks(rows);
-    allow_smem(gd_gradient_rows<T>, sizeof(float) * R * R);
-    gd_gradient_rows<T><<<nb, kRowThreads, sizeof(float) * R * R, s>>>(
-        h->N, static_cast<const T*>(h->F[mode]), h->W32, rows, R, h->grad[mode], h->partials); DF_COUNT();
+    const size_t smem = solve_bytes(R);
+    allow_smem(gd_gradient_rows<T>, smem);
+    gd_gradient_rows<T><<<nb, kT, smem, s>>>(h->N, static_cast<const T*>(h->F[mode]), h->W32, rows,
+                                             R, h->grad[mode], h->partials);
+    DF_COUNT();
     const int tlin = mode == 0 ? kT100 : (mode == 1 ? kT010 : kT001);
-    reduce_scalars<<<1, 32, 0, s>>>(h->partials, (int)nb, 3, h->scal, kG2, tlin,
-                                    mode == 0 ? kT000 : -1); DF_COUNT();
+    gd_scalars<<<1, kT, 0, s>>>(h->partials, (int)nb, h->scal, tlin, mode == 0 ? kT000 : -1);
+    DF_COUNT();
     DF_CUDA(h, cudaGetLastError());
   }
   // R x R matrices of the polynomial: P0 = F^T F, P1 = F^T G + G^T F, P2 = G^T G.
   for (int m = 0; m < 3; ++m) {
     double* P = h->gd_mats + (size_t)m * 3 * R * R;
     DF_CUDA(h, cudaMemcpyAsync(P, h->gram[m], sizeof(double) * R * R, cudaMemcpyDeviceToDevice, s));
-    if ((st = cross_gram<T, float>(h, static_cast<const T*>(h->F[m]), h->grad[m], h->dims[m],
-                                   P + R * R, true)) != DFACTO_OK)
+    if ((st = cross_gram<T, float, false>(h, static_cast<const T*>(h->F[m]), h->grad[m], h->dims[m],
+                                          P + R * R, true)) != DFACTO_OK)
       return st;
-    if ((st = cross_gram<float, float>(h, h->grad[m], h->grad[m], h->dims[m], P + 2 * R * R,
-                                       false)) != DFACTO_OK)
+    if ((st = cross_gram<float, float, true>(h, h->grad[m], h->grad[m], h->dims[m], P + 2 * R * R,
+                                             false)) != DFACTO_OK)
       return st;
   }
   if ((st = dual_pass(h)) != DFACTO_OK) return st;
-  gd_line_search<<<1, 256, 0, s>>>(h->gd_mats, R, h->lambda_reg, h->scal, h->flags + kFlagLsFail); DF_COUNT();
+  gd_line_search<<<1, 256, 0, s>>>(h->gd_mats, R, h->lambda_reg, h->scal, h->flags + kFlagLsFail);
+  DF_COUNT();
   for (int m = 0; m < 3; ++m) {
     const int64_t n = (int64_t)h->dims[m] * R;
-    gd_update<T><<<row_blocks(n, 1024), 256, 0, s>>>(static_cast<T*>(h->F[m]), h->grad[m], n, h->scal); DF_COUNT();
+    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, kMaxBlocks * 4));
+    gd_update<T><<<nb, 256, 0, s>>>(static_cast<T*>(h->F[m]), h->grad[m], n, h->scal);
+    DF_COUNT();
     h->gram_valid[m] = false;
   }
   DF_CUDA(h, cudaGetLastError());

@@ -147,11 +147,22 @@ __global__ void __launch_bounds__(kWalkWarps * 32) dual_walk(const DualParams a)
   }
 }
 
-__global__ void dual_reduce(const double* __restrict__ part, int64_t ncta, double* __restrict__ scal) {
-  if (threadIdx.x < 4) {
-    double s = 0.0;
-    for (int64_t b = 0; b < ncta; ++b) s += part[b * 4 + threadIdx.x];
-    scal[kT110 + threadIdx.x] = s;
+// scal[kT110 + k] = sum over CTAs of part[b][k], k = 0..3 (fixed order:
+// strided per-thread sums, then a fixed tree).
+__global__ void __launch_bounds__(256) dual_reduce(const double* __restrict__ part, int64_t ncta,
+                                                   double* __restrict__ scal) {
+  __shared__ double red[256];
+  for (int k = 0; k < 4; ++k) {
+    double v = 0.0;
+    for (int64_t b = threadIdx.x; b < ncta; b += 256) v += part[b * 4 + k];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) scal[kT110 + k] = red[0];
+    __syncthreads();
   }
 }
 
@@ -210,7 +221,7 @@ dfacto_status dual_pass(dfacto_t* h) {
                       ? launch<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, h->stream)
                       : launch<float>(cfg.vec, cfg.G, a, ncta, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "dual_walk launch");
-  dual_reduce<<<1, 32, 0, h->stream>>>(h->partials, ncta, h->scal); DF_COUNT();
+  dual_reduce<<<1, 256, 0, h->stream>>>(h->partials, ncta, h->scal); DF_COUNT();
   DF_CUDA(h, cudaGetLastError());
   return DFACTO_OK;
 }

@@ -78,6 +78,7 @@ struct dfacto_handle {
   dfacto::ModeCSR m[3];
   void* F[3] = {nullptr, nullptr, nullptr};   // factors, storage dtype
   float* N = nullptr;                         // [max dim x R] MTTKRP output scratch
+  float* Fh = nullptr;                        // [max dim x R] N Gamma^{-1} before normalisation
   float* grad[3] = {nullptr, nullptr, nullptr};  // GD gradients (lazy)
   double* lambda = nullptr;                   // [R]
   float* inv_lambda = nullptr;                // [R] 1/lambda (1 where lambda = 0)
