@@ -58,6 +58,10 @@ def parse_args():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mttkrp-only", action="store_true",
+                    help="profiling driver: only the MTTKRP of each mode, --steps times, on the "
+                         "workload scaled by --phi; prints per-mode times, no contract line")
+    ap.add_argument("--phi", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -410,8 +414,43 @@ def run_ours(args, rank, world, local_rank):
     })
 
 
+def run_mttkrp_only(args):
+    """Per-mode MTTKRP timing on the workload scaled by phi (for profilers)."""
+    import torch
+
+    from paper_1406_4519_gb300 import dfacto, synth
+    wl = WORKLOADS[args.workload]
+    dims, nnz = scaled_replica(wl, args.phi)
+    if wl["zipf"]:
+        idx, val = synth.zipf_tensor(dims, nnz, wl["zipf"], seed=wl["seed"], device="cuda",
+                                     values=wl["values"], R_true=wl["R"])
+    else:
+        idx, val = synth.uniform_tensor(dims, nnz, seed=wl["seed"], device="cuda")
+    R = wl["R"]
+    F0 = synth.normal_factors(dims, R, seed=wl["seed"] + 1, device="cuda")
+    t = dfacto.Tensor(idx, val, dims, rank=R,
+                      factor_dtype=dfacto.BF16 if args.dtype == "bf16" else dfacto.F32)
+    t.set_factors(F0)
+    out = torch.empty(max(dims), R, device="cuda")
+    for mode in range(3):
+        o = out[:dims[mode]]
+        for _ in range(args.warmup):
+            t.mttkrp(mode, o)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            t.mttkrp(mode, o)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": mode, "dims": dims, "nnz": nnz, "rank": R,
+                          "ms": e0.elapsed_time(e1) / max(args.steps, 1)}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.mttkrp_only:
+        run_mttkrp_only(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
