@@ -137,7 +137,7 @@ class ClockSampler:
 def traffic_from_profile(kernel_sha: str):
     """DRAM bytes per launch of the MTTKRP walk from the committed ncu summary,
     if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "mttkrp_walk_c2.md")
+    path = os.path.join(ROOT, "profiles", "mttkrp_walk2_zipf50M_r32.md")
     try:
         text = open(path).read()
     except OSError:
@@ -403,7 +403,7 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic_from_profile(sha),
-                     "kernel": "mttkrp_walk (+ carry fix-up), mean over the three modes",
+                     "kernel": "mttkrp_walk2 (+ carry fix-up), mean over the three modes",
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_mode": alg, "ms_per_mode": mode_ms,
                      "gbs_per_mode": [b / (m * 1e-3) / 1e9 for b, m in zip(alg, mode_ms)]},

@@ -71,6 +71,10 @@ typedef enum dfacto_dtype {
  *                 lets the library choose.  Rounded to a multiple of 32.
  *   vec           factor columns per lane in the MTTKRP kernel (1, 2, 4 or 8;
  *                 must divide R); 0 lets the library choose.
+ *   walk          MTTKRP kernel: 1 detects fiber ends from the fiber pointers
+ *                 as it walks, 2 from a per-nonzero end bitmask and closes the
+ *                 fibers of a few steps together; 0 lets the library choose.
+ *                 Both compute the same sums in the same order.
  */
 typedef struct dfacto_options {
   int32_t rank;
@@ -78,7 +82,8 @@ typedef struct dfacto_options {
   double lambda_reg;
   int32_t seg_nnz;
   int32_t vec;
-  int32_t reserved[6];
+  int32_t walk;
+  int32_t reserved[5];
 } dfacto_options;
 
 /* Sizes of a built tensor. */

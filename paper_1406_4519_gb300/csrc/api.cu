@@ -204,6 +204,7 @@ void dfacto_destroy(dfacto_t* h) {
     cudaFree(M.nz_ptr);
     cudaFree(M.nz_idx);
     cudaFree(M.nz_val);
+    cudaFree(M.end_bits);
     cudaFree(M.seg_fib);
     cudaFree(h->F[m]);
     cudaFree(h->grad[m]);
@@ -251,6 +252,7 @@ dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, co
   if (opt.vec != 0 && (opt.vec != 1 && opt.vec != 2 && opt.vec != 4 && opt.vec != 8)) return DFACTO_EINVAL;
   if (opt.vec != 0 && R % opt.vec != 0) return DFACTO_EINVAL;
   if (opt.seg_nnz < 0) return DFACTO_EINVAL;
+  if (opt.walk < 0 || opt.walk > 2) return DFACTO_EINVAL;
 
   dfacto_t* h = new (std::nothrow) dfacto_handle();
   if (!h) return DFACTO_ENOMEM;
@@ -328,8 +330,10 @@ dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, co
     (void)msg;
     return st;
   }
-  for (int m = 0; m < 3; ++m)
+  for (int m = 0; m < 3; ++m) {
     h->m[m].cfg = choose_walk(R, h->dtype, nnz, h->m[m].nfib, opt.seg_nnz, opt.vec);
+    if (opt.walk > 0) h->m[m].cfg.kernel = opt.walk;
+  }
   if (cudaStreamSynchronize(s) != cudaSuccess) return bail(DFACTO_ECUDA);
   *out = h;
   return DFACTO_OK;

@@ -245,6 +245,16 @@ __global__ void row_pointers(const int32_t* __restrict__ fiber_row, int64_t nfib
   }
 }
 
+// end_bits: bit e set for the last nonzero e of every fiber.
+__global__ void fiber_end_bits(const int64_t* __restrict__ nz_ptr, int64_t nfib,
+                               uint32_t* __restrict__ bits) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nfib; q += stride) {
+    const int64_t e = nz_ptr[q + 1] - 1;
+    atomicOr(bits + (e >> 5), 1u << (e & 31));
+  }
+}
+
 // seg_fib[s] = the fiber holding nonzero s*seg: the last q with nz_ptr[q] <= s*seg.
 __global__ void segment_starts(const int64_t* __restrict__ nz_ptr, int64_t nfib, int64_t nseg,
                                int64_t seg, int32_t* __restrict__ seg_fib) {
@@ -397,6 +407,7 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
       st = dalloc(h, reinterpret_cast<void**>(&M.nz_ptr), sizeof(int64_t));
       if (st == DFACTO_OK) st = dalloc(h, reinterpret_cast<void**>(&M.fiber_idx), sizeof(int32_t));
       if (st == DFACTO_OK) st = dalloc(h, reinterpret_cast<void**>(&M.fiber_row), sizeof(int32_t));
+      if (st == DFACTO_OK) st = dalloc(h, reinterpret_cast<void**>(&M.end_bits), sizeof(uint32_t));
       if (st != DFACTO_OK) return st;
       DF_CUDA(h, cudaMemsetAsync(M.nz_ptr, 0, sizeof(int64_t), s));
       DF_CUDA(h, cudaMemsetAsync(M.fiber_ptr, 0, sizeof(int64_t) * (size_t)(M.dim_o + 1), s));
@@ -453,6 +464,18 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
     scatter_fibers<<<grid_for(n), 256, 0, s>>>(key, perm, n, bf, bi, wide, head, fid, M.nz_ptr,
                                               M.fiber_idx, M.fiber_row, M.nfib); DF_COUNT();
     row_pointers<<<grid_for(M.dim_o + 1), 256, 0, s>>>(M.fiber_row, M.nfib, M.dim_o, M.fiber_ptr); DF_COUNT();
+    {
+      const size_t words = (size_t)((n + 31) / 32);
+      st = dalloc(h, reinterpret_cast<void**>(&M.end_bits), sizeof(uint32_t) * words);
+      if (st != DFACTO_OK) {
+        cleanup();
+        return st;
+      }
+      e = cudaMemsetAsync(M.end_bits, 0, sizeof(uint32_t) * words, s);
+      if (e == cudaSuccess) {
+        fiber_end_bits<<<grid_for(M.nfib), 256, 0, s>>>(M.nz_ptr, M.nfib, M.end_bits); DF_COUNT();
+      }
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) {
       cleanup();

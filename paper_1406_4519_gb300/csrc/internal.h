@@ -18,6 +18,7 @@ struct WalkCfg {
   int vec = 0;    // columns per lane (1, 2, 4, 8)
   int G = 0;      // lanes per group (power of two, G * vec >= R)
   int seg = 0;    // nonzeros per segment (multiple of 32)
+  int kernel = 1; // 1: mttkrp_walk, 2: mttkrp_walk2 (fiber ends from a bitmask)
 };
 
 constexpr int kWalkWarps = 8;  // warps per MTTKRP CTA
@@ -34,6 +35,7 @@ struct ModeCSR {
   int64_t* nz_ptr = nullptr;     // [nfib + 1]
   int32_t* nz_idx = nullptr;     // [nnz]        index `in`
   float* nz_val = nullptr;       // [nnz]
+  uint32_t* end_bits = nullptr;  // [(nnz + 31) / 32] bit p set iff nonzero p ends its fiber
   WalkCfg cfg;
   int64_t nseg = 0;              // segments of cfg.seg nonzeros
   int32_t* seg_fib = nullptr;    // [nseg] fiber holding the first nonzero of each segment

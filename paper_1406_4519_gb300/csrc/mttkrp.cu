@@ -9,6 +9,8 @@ namespace dfacto {
 namespace {
 
 constexpr int kFixThreads = 256;
+constexpr int kFixWarps = kFixThreads / 32;
+constexpr int kAhead = 8;  // carry entries a warp loads before adding them
 
 // One block per CTA c (grid-stride): if c's last partial run belongs to a row r
 // that starts inside c, add up r's partials from CTAs c .. c_last in CTA order
@@ -18,7 +20,7 @@ __global__ void __launch_bounds__(kFixThreads) mttkrp_fixup(
     const int32_t* __restrict__ carry_row, const float* __restrict__ carry,
     const int64_t* __restrict__ fiber_ptr, const int64_t* __restrict__ nz_ptr, float* __restrict__ out,
     int R, int64_t P, int64_t ncta, int64_t dim_o, int32_t* __restrict__ bad) {
-  __shared__ float part[kFixThreads / 32][128];
+  __shared__ float part[kFixWarps][128];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t c = blockIdx.x; c < ncta; c += gridDim.x) {
     const int k = carry_row[2 * c + 1] >= 0 ? 1 : 0;
@@ -32,13 +34,31 @@ __global__ void __launch_bounds__(kFixThreads) mttkrp_fixup(
     float s[kMaxColsPerLane];
 #pragma unroll
     for (int q = 0; q < kMaxColsPerLane; ++q) s[q] = 0.f;
-    for (int64_t j = warp; j < ne; j += kFixThreads / 32) {
-      const int64_t entry = (j == 0) ? (2 * c + k) : (2 * (c + j));
-      if (j > 0 && lane == 0 && carry_row[entry] != r) atomicOr(bad, 1);
+    // Warp w adds entries w, w + 8, w + 16, ... in that order; kAhead of them
+    // are loaded before the adds so that their loads overlap (a row of a few
+    // million nonzeros spans over a thousand CTAs).
+    for (int64_t j0 = warp; j0 < ne; j0 += (int64_t)kAhead * kFixWarps) {
+      float t[kAhead][kMaxColsPerLane];
 #pragma unroll
-      for (int q = 0; q < kMaxColsPerLane; ++q) {
-        const int col = lane + 32 * q;
-        if (col < R) s[q] += carry[entry * R + col];
+      for (int u = 0; u < kAhead; ++u) {
+        const int64_t j = j0 + (int64_t)u * kFixWarps;
+        const int64_t entry = (j == 0) ? (2 * c + k) : (2 * (c + j));
+#pragma unroll
+        for (int q = 0; q < kMaxColsPerLane; ++q) {
+          const int col = lane + 32 * q;
+          t[u][q] = (j < ne && col < R) ? carry[entry * R + col] : 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kAhead; ++u) {
+        if (j0 + (int64_t)u * kFixWarps < ne) {
+#pragma unroll
+          for (int q = 0; q < kMaxColsPerLane; ++q) s[q] += t[u][q];
+        }
+      }
+      if (lane < kAhead) {
+        const int64_t j = j0 + (int64_t)lane * kFixWarps;
+        if (j > 0 && j < ne && carry_row[2 * (c + j)] != r) atomicOr(bad, 1);
       }
     }
 #pragma unroll
@@ -53,7 +73,7 @@ __global__ void __launch_bounds__(kFixThreads) mttkrp_fixup(
         const int col = lane + 32 * q;
         if (col < R) {
           float t = 0.f;
-          for (int w = 0; w < kFixThreads / 32; ++w) t += part[w][col];
+          for (int w = 0; w < kFixWarps; ++w) t += part[w][col];
           out[(int64_t)r * R + col] = t;
         }
       }
@@ -92,12 +112,11 @@ cudaError_t launch_mttkrp_fixup(const int32_t* carry_row, const float* carry,
 WalkCfg choose_walk(int R, int dtype, int64_t nnz, int64_t nfib, int seg_opt, int vec_opt) {
   (void)nnz;
   (void)nfib;
-  (void)dtype;
   WalkCfg c;
-  // Default: eight columns per lane where R allows it -- more segments per
-  // warp means more independent gathers per instruction (measured fastest on
-  // the 50M-nonzero power-law workload at R = 32, FP32 and BF16).
-  int vec = vec_opt > 0 ? vec_opt : 8;
+  // Default: one 16-byte load per lane and factor row (4 FP32 or 8 BF16
+  // columns), measured fastest on the 50M-nonzero power-law workload at
+  // R = 16 and 32.
+  int vec = vec_opt > 0 ? vec_opt : (dtype == DFACTO_BF16 ? 8 : 4);
   while (vec > 1 && (R % vec) != 0) vec >>= 1;
   int G = next_pow2((R + vec - 1) / vec);
   while (G > 32 && vec < 8 && (R % (vec * 2)) == 0) {
@@ -106,6 +125,7 @@ WalkCfg choose_walk(int R, int dtype, int64_t nnz, int64_t nfib, int seg_opt, in
   }
   c.vec = vec;
   c.G = G;
+  c.kernel = 2;  // fiber ends from the end bitmask (faster on every measured shape)
   int seg = seg_opt > 0 ? seg_opt : 128;
   seg = std::max(32, (seg + 31) / 32 * 32);
   c.seg = seg;
@@ -140,6 +160,7 @@ dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out) {
   a.nz_idx = M.nz_idx;
   a.nz_val = M.nz_val;
   a.seg_fib = M.seg_fib;
+  a.end_bits = M.end_bits;
   a.Fin = h->F[M.in];
   a.Ff = h->F[M.f];
   a.out = out;
@@ -152,9 +173,14 @@ dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out) {
   a.seg = cfg.seg;
   if (ncta > 0) {
     const size_t smem = sizeof(float) * (size_t)(2 * segs + 2 * kWalkWarps) * h->R;
-    cudaError_t e = (h->dtype == DFACTO_BF16)
-                        ? launch_walk<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, smem, h->stream)
-                        : launch_walk<float>(cfg.vec, cfg.G, a, ncta, smem, h->stream);
+    cudaError_t e;
+    if (cfg.kernel == 2)
+      e = (h->dtype == DFACTO_BF16) ? launch_walk2<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, h->stream)
+                                    : launch_walk2<float>(cfg.vec, cfg.G, a, ncta, h->stream);
+    else
+      e = (h->dtype == DFACTO_BF16)
+              ? launch_walk<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, smem, h->stream)
+              : launch_walk<float>(cfg.vec, cfg.G, a, ncta, smem, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "mttkrp_walk launch");
   }
   const int64_t zero_blocks = (M.dim_o + kFixThreads - 1) / kFixThreads;

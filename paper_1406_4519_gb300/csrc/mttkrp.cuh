@@ -36,6 +36,7 @@ struct MttkrpParams {
   const int32_t* nz_idx;
   const float* nz_val;
   const int32_t* seg_fib;
+  const uint32_t* end_bits;  // bit p set iff nonzero p ends its fiber (walk2)
   const void* Fin;
   const void* Ff;
   float* out;
@@ -81,6 +82,83 @@ __device__ __forceinline__ void merge_runs(const int32_t* rows, const float* val
     }
   }
   if (run_row >= 0) flush(run_row, run, run_first, true);
+}
+
+// Merge the segment slots of one CTA (s_row/s_val: [SEGS * 2] entries), first
+// inside each warp, then across warps; store complete rows and leave the CTA's
+// partial first/last rows as carries.  Called by all threads after the walk.
+template <int SEGS, int NG>
+__device__ __forceinline__ void mttkrp_merge_cta(const MttkrpParams& a, int32_t* s_row, float* s_val,
+                                                 int32_t* w_row, float* w_val, int lane, int warp,
+                                                 int64_t cta_p0, int64_t cta_p1) {
+  const int R = a.R;
+  // Level 1: each warp merges its NG segments.  Runs strictly inside the
+  // warp's range are complete rows.
+  {
+    if (lane == 0) { w_row[warp * 2] = -1; w_row[warp * 2 + 1] = -1; }
+    __syncwarp();
+    merge_runs(s_row + warp * NG * 2, s_val + (size_t)warp * NG * 2 * R, NG * 2, R, lane,
+               [&](int row, const float (&run)[kMaxColsPerLane], bool first, bool last) {
+                 const int k = first ? 0 : (last ? 1 : -1);
+                 if (k < 0) {
+#pragma unroll
+                   for (int q = 0; q < kMaxColsPerLane; ++q) {
+                     const int col = lane + 32 * q;
+                     if (col < R) a.out[(int64_t)row * R + col] = run[q];
+                   }
+                 } else {
+                   if (lane == 0) w_row[warp * 2 + k] = row;
+#pragma unroll
+                   for (int q = 0; q < kMaxColsPerLane; ++q) {
+                     const int col = lane + 32 * q;
+                     if (col < R) w_val[(size_t)(warp * 2 + k) * R + col] = run[q];
+                   }
+                 }
+               });
+  }
+  __syncthreads();
+
+  // Level 2: warp 0 merges the warps.  The CTA's first run may have started in
+  // an earlier CTA, its last run may continue in a later one.
+  if (warp == 0) {
+    int first_row = -1, last_row = -1;
+    for (int e = 0; e < kWalkWarps * 2; ++e) {
+      const int r = w_row[e];
+      if (r >= 0) { if (first_row < 0) first_row = r; last_row = r; }
+    }
+    bool first_partial = false, last_partial = false;
+    if (first_row >= 0) {
+      // rows of the first and last run: where do they begin and end?
+      const int64_t fb = a.fiber_ptr[first_row];
+      const int64_t le = a.fiber_ptr[last_row + 1];
+      first_partial = a.nz_ptr[fb] < cta_p0;
+      last_partial = a.nz_ptr[le] > cta_p1;
+    }
+    if (lane == 0) {
+      a.carry_row[blockIdx.x * 2] = -1;
+      a.carry_row[blockIdx.x * 2 + 1] = -1;
+    }
+    __syncwarp();
+    merge_runs(w_row, w_val, kWalkWarps * 2, R, lane,
+               [&](int row, const float (&run)[kMaxColsPerLane], bool first, bool last) {
+                 const bool partial = (first && first_partial) || (last && last_partial);
+                 if (!partial) {
+#pragma unroll
+                   for (int q = 0; q < kMaxColsPerLane; ++q) {
+                     const int col = lane + 32 * q;
+                     if (col < R) a.out[(int64_t)row * R + col] = run[q];
+                   }
+                 } else {
+                   const int k = (first && first_partial) ? 0 : 1;
+                   if (lane == 0) a.carry_row[blockIdx.x * 2 + k] = row;
+#pragma unroll
+                   for (int q = 0; q < kMaxColsPerLane; ++q) {
+                     const int col = lane + 32 * q;
+                     if (col < R) a.carry[((int64_t)blockIdx.x * 2 + k) * R + col] = run[q];
+                   }
+                 }
+               });
+  }
 }
 
 // Row of fiber q from row(M^r) alone: the largest r < dim_o with
@@ -299,6 +377,196 @@ __global__ void __launch_bounds__(kWalkWarps * 32) mttkrp_walk(const MttkrpParam
   }
 }
 
+// ---------------------------------------------------------------------------
+// mttkrp_walk2: the same walk with fiber ends taken from a bitmask and fibers
+// closed in batches.  Per sub-batch of U steps a group
+//   (1) gathers the U F_in rows,
+//   (2) accumulates v over the U nonzeros; where a bit of end_bits marks the
+//       last nonzero of a fiber, v is parked in a per-lane shared-memory slot
+//       and restarted (no branch on fiber metadata in this loop),
+//   (3) closes the k <= U fibers that ended: loads their f and row, issues all
+//       k F_f gathers at once, then folds v_j (*) F_f[f_j] into the row sums.
+// The merge of rows shared between segments, warps and CTAs is the one of
+// mttkrp_walk.
+// ---------------------------------------------------------------------------
+template <typename T, int VEC, int G>
+struct Walk2Shape {
+  static constexpr int NG = 32 / G;
+  static constexpr int SEGS = kWalkWarps * NG;
+  static constexpr int U = (G < 32 / VEC) ? G : (32 / VEC);
+  // Resident CTAs per SM the register budget is cut for: the kernel is bound by
+  // the latency of its gathers, so occupancy pays more than a few spilled
+  // registers.  With U * VEC <= 16 gathered values per lane it fits 64
+  // registers (4 CTAs), otherwise 80 (3 CTAs).
+  static constexpr int MIN_BLOCKS = (U * VEC <= 16) ? 4 : 3;
+  static size_t smem_bytes(int R) {
+    return sizeof(float) * ((size_t)(2 * SEGS + 2 * kWalkWarps) * R + (size_t)kWalkWarps * 32 * U * VEC);
+  }
+};
+
+template <typename T, int VEC, int G>
+__global__ void __launch_bounds__(kWalkWarps * 32, (Walk2Shape<T, VEC, G>::MIN_BLOCKS))
+    mttkrp_walk2(const MttkrpParams a) {
+  using Shape = Walk2Shape<T, VEC, G>;
+  constexpr int NG = Shape::NG, SEGS = Shape::SEGS, U = Shape::U;
+  constexpr int NT = kWalkWarps * 32;
+  extern __shared__ __align__(16) float smem[];
+  const int R = a.R;
+  float* s_val = smem;                           // [SEGS * 2][R]
+  float* w_val = smem + (size_t)SEGS * 2 * R;    // [kWalkWarps * 2][R]
+  float* vb = w_val + (size_t)kWalkWarps * 2 * R;  // [U][VEC][NT] parked fiber sums
+  __shared__ int32_t s_row[SEGS * 2];
+  __shared__ int32_t w_row[kWalkWarps * 2];
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int g = lane / G, c = lane % G;
+  const int gbase = g * G;
+  const int col0 = c * VEC;
+  const bool colok = col0 < R;
+  const int sl = warp * NG + g;
+  const int nnz = (int)a.nnz;
+  const int cta_p0 = (int)min((int64_t)blockIdx.x * SEGS * a.seg, a.nnz);
+  const int cta_p1 = (int)min((int64_t)cta_p0 + (int64_t)SEGS * a.seg, a.nnz);
+  const int p0 = (int)min((int64_t)cta_p0 + (int64_t)sl * a.seg, a.nnz);
+  const int p1 = min(p0 + a.seg, nnz);
+  const bool active = p0 < nnz;
+  const T* __restrict__ Fin = static_cast<const T*>(a.Fin);
+  const T* __restrict__ Ff = static_cast<const T*>(a.Ff);
+
+  float v[VEC], acc[VEC];
+#pragma unroll
+  for (int k = 0; k < VEC; ++k) { v[k] = 0.f; acc[k] = 0.f; }
+  int q = 0;          // fiber holding the current nonzero
+  int row_cur = -1;
+  if (active) {
+    q = a.seg_fib[(int64_t)blockIdx.x * SEGS + sl];
+    row_cur = a.fiber_row[q];
+  }
+  bool head_open = true;
+  auto put_slot = [&](int k, int row, const float (&val)[VEC]) {
+    if (c == 0) s_row[sl * 2 + k] = row;
+    if (colok) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) s_val[(size_t)(sl * 2 + k) * R + col0 + e] = val[e];
+    }
+  };
+  // Fold w = vv (*) ff of a fiber of row r into the row sums (emitting the
+  // previous row when r starts a new one).
+  auto fold = [&](int r, const float (&vv)[VEC], const float (&ff)[VEC]) {
+    if (r != row_cur) {
+      if (head_open) {
+        put_slot(0, row_cur, acc);
+        head_open = false;
+      } else if (colok) {
+        VecIO<float, VEC>::store(a.out + (int64_t)row_cur * R + col0, acc);
+      }
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) acc[e] = 0.f;
+      row_cur = r;
+    }
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = fmaf(vv[e], ff[e], acc[e]);
+  };
+
+  for (int base = p0; base < p0 + a.seg; base += G) {
+    const int pl = base + c;
+    const bool okl = pl < p1;
+    const int my_in = okl ? __ldg(a.nz_idx + pl) : 0;
+    const float my_x = okl ? __ldg(a.nz_val + pl) : 0.f;
+    // end bits of the batch's G positions (base is a multiple of G, G | 32)
+    const uint32_t ebits = active ? (__ldg(a.end_bits + (base >> 5)) >> (base & 31)) : 0u;
+#pragma unroll
+    for (int u0 = 0; u0 < G; u0 += U) {
+      float fin[U][VEC];
+#pragma unroll
+      for (int uu = 0; uu < U; ++uu) {
+        const int in = __shfl_sync(kFull, my_in, gbase + u0 + uu);
+        if (colok && base + u0 + uu < p1) {
+          VecIO<T, VEC>::load(Fin + (int64_t)in * R + col0, fin[uu]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) fin[uu][e] = 0.f;
+        }
+      }
+      int k = 0;  // fibers closed in this sub-batch
+#pragma unroll
+      for (int uu = 0; uu < U; ++uu) {
+        const float x = __shfl_sync(kFull, my_x, gbase + u0 + uu);
+        const int p = base + u0 + uu;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) v[e] = fmaf(x, fin[uu][e], v[e]);
+        const bool end = p < p1 && ((ebits >> (u0 + uu)) & 1u);
+        if (end) {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) {
+            vb[((size_t)k * VEC + e) * NT + tid] = v[e];
+            v[e] = 0.f;
+          }
+        }
+        k += end ? 1 : 0;
+      }
+      // Close the k fibers q .. q + k - 1.
+      if (k > 0) {
+        int fj[U], rj[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          fj[j] = 0;
+          rj[j] = row_cur;
+          if (j < k) {
+            fj[j] = __ldg(a.fiber_idx + q + j);
+            rj[j] = __ldg(a.fiber_row + q + j);
+          }
+        }
+        float ff[U][VEC];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          if (j < k && colok) {
+            VecIO<T, VEC>::load(Ff + (int64_t)fj[j] * R + col0, ff[j]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) ff[j][e] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          if (j < k) {
+            float vv[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) vv[e] = vb[((size_t)j * VEC + e) * NT + tid];
+            fold(rj[j], vv, ff[j]);
+          }
+        }
+        q += k;
+      }
+    }
+  }
+  // The fiber open at the segment end (if its last nonzero lies beyond p1).
+  if (active && !((__ldg(a.end_bits + ((p1 - 1) >> 5)) >> ((p1 - 1) & 31)) & 1u)) {
+    const int f = __ldg(a.fiber_idx + q);
+    const int r = __ldg(a.fiber_row + q);
+    float ff[VEC];
+    if (colok) VecIO<T, VEC>::load(Ff + (int64_t)f * R + col0, ff);
+    else {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) ff[e] = 0.f;
+    }
+    fold(r, v, ff);
+  }
+
+  // Segment slots: 0 = head row partial, 1 = tail row partial (-1 = none).
+  if (!active) {
+    if (c == 0) { s_row[sl * 2] = -1; s_row[sl * 2 + 1] = -1; }
+  } else if (head_open) {
+    put_slot(0, row_cur, acc);
+    if (c == 0) s_row[sl * 2 + 1] = -1;
+  } else {
+    put_slot(1, row_cur, acc);
+  }
+  __syncthreads();
+  mttkrp_merge_cta<SEGS, NG>(a, s_row, s_val, w_row, w_val, lane, warp, cta_p0, cta_p1);
+}
+
 // Launchers of the carry fix-up (mttkrp.cu) and of the segment-start search
 // (build.cu), shared with the allocation-free entry point.
 cudaError_t launch_mttkrp_fixup(const int32_t* carry_row, const float* carry,
@@ -312,5 +580,7 @@ cudaError_t launch_segment_starts(const int64_t* nz_ptr, int64_t nfib, int64_t n
 template <typename T>
 cudaError_t launch_walk(int vec, int G, const MttkrpParams& a, int64_t ncta, size_t smem,
                         cudaStream_t s);
+template <typename T>
+cudaError_t launch_walk2(int vec, int G, const MttkrpParams& a, int64_t ncta, cudaStream_t s);
 
 }  // namespace dfacto

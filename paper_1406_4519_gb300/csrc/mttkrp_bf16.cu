@@ -32,4 +32,31 @@ cudaError_t launch_walk<__nv_bfloat16>(int vec, int G, const MttkrpParams& a, in
   return cudaErrorInvalidValue;
 }
 
+template <int VEC, int G>
+static cudaError_t go2(const MttkrpParams& a, int64_t ncta, cudaStream_t s) {
+  auto k = mttkrp_walk2<__nv_bfloat16, VEC, G>;
+  const size_t smem = Walk2Shape<__nv_bfloat16, VEC, G>::smem_bytes(a.R);
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  k<<<(unsigned)ncta, kWalkWarps * 32, smem, s>>>(a);
+  DF_COUNT();
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_walk2<__nv_bfloat16>(int vec, int G, const MttkrpParams& a, int64_t ncta, cudaStream_t s) {
+#define DF_CASE(V, GG) \
+  if (vec == V && G == GG) return go2<V, GG>(a, ncta, s);
+  DF_CASE(1, 1) DF_CASE(1, 2) DF_CASE(1, 4) DF_CASE(1, 8) DF_CASE(1, 16) DF_CASE(1, 32)
+  DF_CASE(2, 1) DF_CASE(2, 2) DF_CASE(2, 4) DF_CASE(2, 8) DF_CASE(2, 16) DF_CASE(2, 32)
+  DF_CASE(4, 1) DF_CASE(4, 2) DF_CASE(4, 4) DF_CASE(4, 8) DF_CASE(4, 16) DF_CASE(4, 32)
+  DF_CASE(8, 1) DF_CASE(8, 2) DF_CASE(8, 4) DF_CASE(8, 8) DF_CASE(8, 16)
+#undef DF_CASE
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace dfacto

@@ -79,8 +79,9 @@ extern "C" dfacto_status dfacto_mttkrp_noalloc(const dfacto_csr_view* csr, const
     return DFACTO_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-  // The same walk configuration dfacto_mttkrp uses for FP32 factors.
-  const WalkCfg cfg = choose_walk(R, DFACTO_F32, nnz, nfib, 0, 0);
+  // Eight columns per lane where R allows it: 64 segments per block, which
+  // fixes the scratch per nonzero stated in the header.
+  const WalkCfg cfg = choose_walk(R, DFACTO_F32, nnz, nfib, 0, 8);
   const int segs = kWalkWarps * (32 / cfg.G);
   const int64_t P = (int64_t)segs * cfg.seg;
   const int64_t ncta = (nnz + P - 1) / P;

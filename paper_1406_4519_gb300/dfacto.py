@@ -34,7 +34,8 @@ class DfactoError(RuntimeError):
 class dfacto_options(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int32), ("factor_dtype", ctypes.c_int32),
                 ("lambda_reg", ctypes.c_double), ("seg_nnz", ctypes.c_int32),
-                ("vec", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("vec", ctypes.c_int32), ("walk", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class dfacto_info(ctypes.Structure):
@@ -115,13 +116,14 @@ def _stream_ptr(stream) -> Optional[int]:
 
 
 def dfacto_options_init(rank: int, factor_dtype: int = F32, lambda_reg: float = 0.0,
-                        seg_nnz: int = 0, vec: int = 0) -> dfacto_options:
+                        seg_nnz: int = 0, vec: int = 0, walk: int = 0) -> dfacto_options:
     opt = dfacto_options()
     load().dfacto_options_init(ctypes.byref(opt), int(rank))
     opt.factor_dtype = factor_dtype
     opt.lambda_reg = float(lambda_reg)
     opt.seg_nnz = int(seg_nnz)
     opt.vec = int(vec)
+    opt.walk = int(walk)
     return opt
 
 
@@ -273,10 +275,11 @@ class Tensor:
     """Owning wrapper of a dfacto handle (destroyed with the object)."""
 
     def __init__(self, idx, val, dims, rank: int, factor_dtype: int = F32,
-                 lambda_reg: float = 0.0, seg_nnz: int = 0, vec: int = 0, stream=None):
+                 lambda_reg: float = 0.0, seg_nnz: int = 0, vec: int = 0, walk: int = 0,
+                 stream=None):
         self.dims = [int(d) for d in dims]
         self.rank = int(rank)
-        self.opt = dfacto_options_init(rank, factor_dtype, lambda_reg, seg_nnz, vec)
+        self.opt = dfacto_options_init(rank, factor_dtype, lambda_reg, seg_nnz, vec, walk)
         self.h = dfacto_build(idx, val, dims, self.opt, stream)
 
     def __del__(self):

@@ -47,8 +47,9 @@ def test_struct_layouts_match_header(tmp_path, lib):
 #include <stddef.h>
 #include "dfacto.h"
 int main(void) {
-  printf("%zu %zu %zu %zu\\n", sizeof(dfacto_options), offsetof(dfacto_options, lambda_reg),
-         offsetof(dfacto_options, seg_nnz), offsetof(dfacto_options, vec));
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(dfacto_options), offsetof(dfacto_options, lambda_reg),
+         offsetof(dfacto_options, seg_nnz), offsetof(dfacto_options, vec),
+         offsetof(dfacto_options, walk));
   printf("%zu %zu %zu %zu\\n", sizeof(dfacto_info), offsetof(dfacto_info, nnz),
          offsetof(dfacto_info, norm_x2), offsetof(dfacto_info, vec));
   printf("%zu %zu\\n", sizeof(dfacto_csr_view), offsetof(dfacto_csr_view, nz_val));
@@ -60,6 +61,7 @@ int main(void) {
     got = subprocess.check_output([str(exe)]).decode().split()
     want = [ctypes.sizeof(dfacto.dfacto_options), dfacto.dfacto_options.lambda_reg.offset,
             dfacto.dfacto_options.seg_nnz.offset, dfacto.dfacto_options.vec.offset,
+            dfacto.dfacto_options.walk.offset,
             ctypes.sizeof(dfacto.dfacto_info), dfacto.dfacto_info.nnz.offset,
             dfacto.dfacto_info.norm_x2.offset, dfacto.dfacto_info.vec.offset,
             ctypes.sizeof(dfacto.dfacto_csr_view), dfacto.dfacto_csr_view.nz_val.offset]

@@ -34,13 +34,13 @@ def as_oracle(idx, val, dims):
     return oracle.Tensor(idx.cpu().numpy(), val.cpu().numpy(), dims)
 
 
-def make(dims, nnz, R, seed, dtype=dfacto.F32, seg=0, vec=0, zipf=None, values="uniform"):
+def make(dims, nnz, R, seed, dtype=dfacto.F32, seg=0, vec=0, zipf=None, values="uniform", walk=0):
     if zipf is None:
         idx, val = synth.uniform_tensor(dims, nnz, seed=seed, device="cuda")
     else:
         idx, val = synth.zipf_tensor(dims, nnz, zipf, seed=seed, device="cuda", values=values)
     F = synth.normal_factors(dims, R, seed=seed + 1, device="cuda")
-    t = dfacto.Tensor(idx, val, dims, rank=R, factor_dtype=dtype, seg_nnz=seg, vec=vec)
+    t = dfacto.Tensor(idx, val, dims, rank=R, factor_dtype=dtype, seg_nnz=seg, vec=vec, walk=walk)
     t.set_factors(F)
     return t, idx, val, F
 
@@ -119,11 +119,12 @@ def test_mttkrp_appendix_d_exact():
     np.testing.assert_array_equal(t.mttkrp(0).cpu().numpy(), g["M"])
 
 
+@pytest.mark.parametrize("walk", [1, 2])
 @pytest.mark.parametrize("R", [1, 3, 8, 10, 16, 32, 64])
 @pytest.mark.parametrize("seg", [32, 256])
-def test_mttkrp_uniform(R, seg):
+def test_mttkrp_uniform(R, seg, walk):
     dims = [50, 40, 30]
-    t, idx, val, F = make(dims, 20000, R, seed=100 + R, seg=seg)
+    t, idx, val, F = make(dims, 20000, R, seed=100 + R, seg=seg, walk=walk)
     ot = as_oracle(idx, val, dims)
     Fh = [host(f) for f in F]
     for mode in range(3):
@@ -131,23 +132,25 @@ def test_mttkrp_uniform(R, seg):
         assert err <= MTTKRP_TOL, (mode, err)
 
 
+@pytest.mark.parametrize("walk", [1, 2])
 @pytest.mark.parametrize("vec", [1, 2, 4, 8])
-def test_mttkrp_lane_layouts(vec):
+def test_mttkrp_lane_layouts(vec, walk):
     dims = [300, 200, 100]
-    t, idx, val, F = make(dims, 30000, 32, seed=200 + vec, seg=64, vec=vec)
+    t, idx, val, F = make(dims, 30000, 32, seed=200 + vec, seg=64, vec=vec, walk=walk)
     ot = as_oracle(idx, val, dims)
     Fh = [host(f) for f in F]
     for mode in range(3):
         assert rel(host(t.mttkrp(mode)), oracle.mttkrp(ot, mode, Fh)) <= MTTKRP_TOL
 
 
+@pytest.mark.parametrize("walk", [1, 2])
 @pytest.mark.parametrize("seg", [32, 128, 1024])
-def test_mttkrp_power_law_rows_span_many_ctas(seg):
+def test_mttkrp_power_law_rows_span_many_ctas(seg, walk):
     """Zipf heads put ~10% of all nonzeros in one row and long fibers across
     many segments and CTAs: the carry merge must still be exact in order."""
     dims = [2000, 1000, 500]
     t, idx, val, F = make(dims, 300000, 16, seed=300, seg=seg, zipf=[1.2, 1.2, 1.2],
-                          values="cp")
+                          values="cp", walk=walk)
     ot = as_oracle(idx, val, dims)
     Fh = [host(f) for f in F]
     for mode in range(3):
@@ -162,8 +165,8 @@ def test_mttkrp_single_row_and_single_fiber():
     val = torch.rand(J, generator=torch.Generator().manual_seed(1)).cuda()
     dims = [4, J, 5]
     F = synth.normal_factors(dims, 8, seed=9, device="cuda")
-    for seg in (32, 256):
-        t = dfacto.Tensor(idx, val, dims, rank=8, seg_nnz=seg)
+    for seg, walk in ((32, 1), (256, 1), (32, 2), (256, 2)):
+        t = dfacto.Tensor(idx, val, dims, rank=8, seg_nnz=seg, walk=walk)
         t.set_factors(F)
         ot = as_oracle(idx, val, dims)
         for mode in range(3):
@@ -192,20 +195,26 @@ def test_mttkrp_empty_tensor_and_empty_rows():
 
 def test_mttkrp_is_bitwise_deterministic():
     dims = [2000, 1000, 500]
-    t, idx, val, F = make(dims, 200000, 32, seed=400, seg=32, zipf=[1.2, 1.2, 1.2])
+    t, idx, val, F = make(dims, 200000, 32, seed=400, seg=32, zipf=[1.2, 1.2, 1.2], walk=1)
+    t2 = dfacto.Tensor(idx, val, dims, rank=32, seg_nnz=32, walk=2)
+    t2.set_factors(F)
     for mode in range(3):
         a = t.mttkrp(mode).clone()
         b = t.mttkrp(mode).clone()
         assert torch.equal(a.view(torch.int32), b.view(torch.int32))
+        # both walks add the same terms in the same order
+        c2 = t2.mttkrp(mode).clone()
+        assert torch.equal(a.view(torch.int32), c2.view(torch.int32))
 
 
+@pytest.mark.parametrize("walk", [1, 2])
 @pytest.mark.parametrize("R", [8, 10, 16, 32])
-def test_mttkrp_bf16_factors(R):
+def test_mttkrp_bf16_factors(R, walk):
     dims = [400, 300, 200]
     idx, val = synth.zipf_tensor(dims, 60000, [1.2, 1.2, 1.2], seed=500 + R, device="cuda",
                                  values="uniform")
     F = synth.normal_factors(dims, R, seed=R, device="cuda")
-    t = dfacto.Tensor(idx, val, dims, rank=R, factor_dtype=dfacto.BF16)
+    t = dfacto.Tensor(idx, val, dims, rank=R, factor_dtype=dfacto.BF16, walk=walk)
     t.set_factors(F)
     ot = as_oracle(idx, val, dims)
     F32 = [host(f) for f in F]
