@@ -285,6 +285,100 @@ dfacto_status dfacto_get_csr(dfacto_t* h, int mode, dfacto_csr_view* view);
 dfacto_status dfacto_mttkrp_noalloc(const dfacto_csr_view* csr, const float* F_in, const float* F_f,
                                     int32_t R, float* out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent decompositions advanced together.
+ *
+ * The paper factorizes one tensor at a time; a batch runs the ALS sweep of
+ * Algorithm 4 (with the MTTKRP of Algorithm 1) for n independent jobs at
+ * once.  Jobs that share (R, factor type) form a rank class: their flattened
+ * CSR copies are concatenated into one block-diagonal tensor (indices offset
+ * per job) and their factors are pooled, so the MTTKRP of a mode for every
+ * job of every class is one persistent kernel launch.  The per-job R x R
+ * steps (Gamma^{-1}, normalisation, Grams, fit) run as parallel branches, and
+ * from the second sweep on the whole sweep is replayed as one CUDA graph.
+ * ------------------------------------------------------------------------ */
+typedef struct dfacto_batch dfacto_batch_t;
+
+typedef struct {
+  int32_t side_streams; /* parallel branches for the per-job steps (0: 16) */
+  int32_t use_graph;    /* nonzero: capture the sweep into a CUDA graph and
+                           replay it from the second sweep on */
+  int32_t autotune;     /* nonzero: time walk shapes per rank class at creation */
+  int32_t reserved[5];  /* zero */
+} dfacto_batch_options;
+
+/* Defaults: 16 side streams, graph on, autotune on. */
+void dfacto_batch_options_init(dfacto_batch_options* opt);
+
+/*
+ * dfacto_batch_create -- group n built handles (dfacto_build, factors set)
+ * into a batch.
+ *   jobs    host array of n distinct handles on the current device, none in
+ *           another batch.  The batch borrows them: their factors move into
+ *           the batch's pools (the handles keep working, with their factor
+ *           pointers inside the pools) until dfacto_batch_destroy moves them
+ *           back.  Destroy the batch before its jobs; a job destroyed first
+ *           leaves the batch unusable (its calls return DFACTO_EINVAL).
+ *   n       1..65536.
+ *   opt     options, or NULL for the defaults.
+ *   stream  cudaStream_t the batch's work is ordered after and that
+ *           dfacto_batch_sync waits for (NULL: the legacy default stream).
+ *           The batch forks its own non-blocking streams from it.
+ * The batch owns a second copy of every job's CSR arrays (concatenated per
+ * rank class) and one MTTKRP output buffer per class and mode.  Returns
+ * DFACTO_EINVAL for bad arguments, DFACTO_ENOMEM, DFACTO_ECUDA.  Synchronous.
+ */
+dfacto_status dfacto_batch_create(dfacto_t* const* jobs, int32_t n, const dfacto_batch_options* opt,
+                                  void* stream, dfacto_batch_t** out);
+
+/* Free the batch's memory, streams and graph and hand the factors back to
+ * the jobs (copied into allocations of their own).  NULL is ignored. */
+void dfacto_batch_destroy(dfacto_batch_t* b);
+
+/*
+ * dfacto_batch_mttkrp -- the MTTKRP of mode `mode` (Algorithm 1) for every
+ * job, from the jobs' current factors.
+ *   out     host array of n device pointers; out[j] is float[dims_j[mode] x
+ *           R_j], row-major, written completely.
+ * Asynchronous on the batch stream.
+ */
+dfacto_status dfacto_batch_mttkrp(dfacto_batch_t* b, int mode, float* const* out);
+
+/*
+ * dfacto_batch_als_iter -- one ALS sweep (Algorithm 4: modes 1, 2, 3) for
+ * every job, then every job's fit.  The first sweep (and any sweep after a
+ * job's factors were changed outside the batch) is issued launch by launch;
+ * later sweeps replay the captured graph.
+ *   fits    host double[n] or NULL: fit of each job after the sweep (the
+ *           call then waits for the sweep).
+ * Returns DFACTO_ESINGULAR (informational) if any job's Gamma needed the
+ * pseudo-inverse, DFACTO_EINTERNAL if a consistency check failed.
+ */
+dfacto_status dfacto_batch_als_iter(dfacto_batch_t* b, double* fits);
+
+/* Wait for all work of the batch. */
+dfacto_status dfacto_batch_sync(dfacto_batch_t* b);
+
+/* One rank class of a batch: its jobs share rank and factor type. */
+typedef struct {
+  int32_t rank;
+  int32_t factor_dtype;
+  int32_t n_jobs;
+  int32_t vec;       /* columns per lane of the walk */
+  int32_t lanes;     /* lanes per segment (G); a warp walks 32 / lanes segments */
+  int32_t seg_nnz;   /* nonzeros per segment */
+  int64_t nnz;       /* nonzeros of the class (all its jobs) */
+  double tuned_ms;   /* MTTKRP time of the three modes at the chosen shape
+                        (0 when not tuned) */
+} dfacto_batch_class;
+
+/* Number of rank classes, and class k's description (0 <= k < classes). */
+int32_t dfacto_batch_num_classes(const dfacto_batch_t* b);
+dfacto_status dfacto_batch_get_class(const dfacto_batch_t* b, int32_t k, dfacto_batch_class* out);
+
+/* Message of the last failure on b (empty if none). */
+const char* dfacto_batch_last_error(const dfacto_batch_t* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -196,6 +196,10 @@ const char* dfacto_status_str(dfacto_status s) {
 void dfacto_destroy(dfacto_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  if (h->batch) {  // the factors belong to the batch's pools
+    batch_forget(h->batch, h);
+    for (int m = 0; m < 3; ++m) h->F[m] = nullptr;
+  }
   for (int m = 0; m < 3; ++m) {
     ModeCSR& M = h->m[m];
     cudaFree(M.fiber_ptr);

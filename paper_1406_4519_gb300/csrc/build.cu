@@ -316,6 +316,17 @@ cudaError_t launch_segment_starts(const int64_t* nz_ptr, int64_t nfib, int64_t n
   return cudaGetLastError();
 }
 
+cudaError_t launch_fiber_end_bits(const int64_t* nz_ptr, int64_t nfib, int64_t nnz, uint32_t* bits,
+                                  cudaStream_t s) {
+  const size_t words = (size_t)((nnz + 31) / 32);
+  if (words == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(uint32_t) * words, s);
+  if (e != cudaSuccess || nfib <= 0) return e;
+  fiber_end_bits<<<grid_for(nfib), 256, 0, s>>>(nz_ptr, nfib, bits);
+  DF_COUNT();
+  return cudaGetLastError();
+}
+
 dfacto_status ensure_segments(dfacto_t* h, int mode) {
   ModeCSR& M = h->m[mode];
   const int seg = M.cfg.seg;

@@ -873,21 +873,16 @@ dfacto_status gram_of_factor(dfacto_t* h, int m) {
 namespace {
 
 template <typename T>
-dfacto_status als_mode_T(dfacto_t* h, int mode) {
+dfacto_status als_post_T(dfacto_t* h, int mode, float* N) {
   const ModeCSR& M = h->m[mode];
   const int R = h->R;
   const int R4 = (R + 3) / 4;
   cudaStream_t s = h->stream;
-  dfacto_status st;
-  for (int m : {M.f, M.in})
-    if (!h->gram_valid[m] && (st = gram_of_factor(h, m)) != DFACTO_OK) return st;
-  if ((st = launch_gamma_inverse(h, h->gram[M.f], h->gram[M.in])) != DFACTO_OK) return st;
-  if ((st = mttkrp_launch(h, mode, h->N)) != DFACTO_OK) return st;
   const int64_t rows = M.dim_o;
   const unsigned nb = row_blocks(rows);
   const size_t smem_a = solve_bytes(R);
   allow_smem(als_solve_rows, smem_a);
-  als_solve_rows<<<nb, kT, smem_a, s>>>(h->N, h->W32, rows, R, h->Fh, h->partials);
+  als_solve_rows<<<nb, kT, smem_a, s>>>(N, h->W32, rows, R, h->Fh, h->partials);
   DF_COUNT();
   finish_lambda<<<R, kT, 0, s>>>(h->partials, (int)nb, R, h->lambda, h->inv_lambda);
   DF_COUNT();
@@ -897,11 +892,11 @@ dfacto_status als_mode_T(dfacto_t* h, int mode) {
   if (R4 * R4 <= kT) {
     allow_smem(als_store_rows<T, 1>, smem_b);
     als_store_rows<T, 1><<<nb, kT, smem_b, s>>>(h->Fh, h->inv_lambda, h->lambda, rows, R, F,
-                                                h->partials, last ? h->N : nullptr, h->ipart);
+                                                h->partials, last ? N : nullptr, h->ipart);
   } else {
     allow_smem(als_store_rows<T, 4>, smem_b);
     als_store_rows<T, 4><<<nb, kT, smem_b, s>>>(h->Fh, h->inv_lambda, h->lambda, rows, R, F,
-                                                h->partials, last ? h->N : nullptr, h->ipart);
+                                                h->partials, last ? N : nullptr, h->ipart);
   }
   DF_COUNT();
   reduce_partials<<<(R * R + 31) / 32, kT, 0, s>>>(h->partials, (int)nb, R * R, R, false,
@@ -915,8 +910,27 @@ dfacto_status als_mode_T(dfacto_t* h, int mode) {
 
 }  // namespace
 
+// Steps of Algorithm 2 for one mode before the MTTKRP: the Grams of the other
+// two factors (when not already known) and Gamma^{-1}.
+dfacto_status als_pre(dfacto_t* h, int mode) {
+  const ModeCSR& M = h->m[mode];
+  dfacto_status st;
+  for (int m : {M.f, M.in})
+    if (!h->gram_valid[m] && (st = gram_of_factor(h, m)) != DFACTO_OK) return st;
+  return launch_gamma_inverse(h, h->gram[M.f], h->gram[M.in]);
+}
+
+// Steps after the MTTKRP N of this mode: N Gamma^{-1}, normalisation, store,
+// and the Gram of the new factor (plus the fit's inner product on mode 3).
+dfacto_status als_post(dfacto_t* h, int mode, float* N) {
+  return h->dtype == DFACTO_BF16 ? als_post_T<__nv_bfloat16>(h, mode, N) : als_post_T<float>(h, mode, N);
+}
+
 dfacto_status als_mode(dfacto_t* h, int mode) {
-  return h->dtype == DFACTO_BF16 ? als_mode_T<__nv_bfloat16>(h, mode) : als_mode_T<float>(h, mode);
+  dfacto_status st = als_pre(h, mode);
+  if (st == DFACTO_OK) st = mttkrp_launch(h, mode, h->N);
+  if (st == DFACTO_OK) st = als_post(h, mode, h->N);
+  return st;
 }
 
 dfacto_status als_fit(dfacto_t* h) {

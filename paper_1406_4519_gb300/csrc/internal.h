@@ -103,6 +103,9 @@ struct dfacto_handle {
   int32_t* host_flags = nullptr;              // pinned mirror of flags
   int64_t bytes = 0;
   std::string err;
+  // Set while the handle is in a batch: F[m] then point into the batch's
+  // factor pools and are not the handle's to free.
+  dfacto_batch* batch = nullptr;
 };
 
 namespace dfacto {
@@ -139,9 +142,15 @@ dfacto_status ensure_segments(dfacto_t* h, int mode);
 WalkCfg choose_walk(int R, int dtype, int64_t nnz, int64_t nfib, int seg_opt, int vec_opt);
 dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out);
 
+// ---- batches (batch.cu) ---------------------------------------------------
+// Called by dfacto_destroy for a handle still in a batch: the batch drops it.
+void batch_forget(dfacto_batch* b, dfacto_t* h);
+
 // ---- dense R x R and row-wise kernels (dense.cu) --------------------------
 dfacto_status gram_of_factor(dfacto_t* h, int m);
 dfacto_status als_mode(dfacto_t* h, int mode);
+dfacto_status als_pre(dfacto_t* h, int mode);
+dfacto_status als_post(dfacto_t* h, int mode, float* N);
 dfacto_status als_fit(dfacto_t* h);
 dfacto_status fit_direct(dfacto_t* h);
 dfacto_status gd_step(dfacto_t* h);

@@ -88,9 +88,9 @@ __device__ __forceinline__ void merge_runs(const int32_t* rows, const float* val
 // inside each warp, then across warps; store complete rows and leave the CTA's
 // partial first/last rows as carries.  Called by all threads after the walk.
 template <int SEGS, int NG>
-__device__ __forceinline__ void mttkrp_merge_cta(const MttkrpParams& a, int32_t* s_row, float* s_val,
-                                                 int32_t* w_row, float* w_val, int lane, int warp,
-                                                 int64_t cta_p0, int64_t cta_p1) {
+__device__ __forceinline__ void mttkrp_merge_cta(const MttkrpParams& a, int cta, int32_t* s_row,
+                                                 float* s_val, int32_t* w_row, float* w_val, int lane,
+                                                 int warp, int64_t cta_p0, int64_t cta_p1) {
   const int R = a.R;
   // Level 1: each warp merges its NG segments.  Runs strictly inside the
   // warp's range are complete rows.
@@ -135,8 +135,8 @@ __device__ __forceinline__ void mttkrp_merge_cta(const MttkrpParams& a, int32_t*
       last_partial = a.nz_ptr[le] > cta_p1;
     }
     if (lane == 0) {
-      a.carry_row[blockIdx.x * 2] = -1;
-      a.carry_row[blockIdx.x * 2 + 1] = -1;
+      a.carry_row[cta * 2] = -1;
+      a.carry_row[cta * 2 + 1] = -1;
     }
     __syncwarp();
     merge_runs(w_row, w_val, kWalkWarps * 2, R, lane,
@@ -150,11 +150,11 @@ __device__ __forceinline__ void mttkrp_merge_cta(const MttkrpParams& a, int32_t*
                    }
                  } else {
                    const int k = (first && first_partial) ? 0 : 1;
-                   if (lane == 0) a.carry_row[blockIdx.x * 2 + k] = row;
+                   if (lane == 0) a.carry_row[cta * 2 + k] = row;
 #pragma unroll
                    for (int q = 0; q < kMaxColsPerLane; ++q) {
                      const int col = lane + 32 * q;
-                     if (col < R) a.carry[((int64_t)blockIdx.x * 2 + k) * R + col] = run[q];
+                     if (col < R) a.carry[((int64_t)cta * 2 + k) * R + col] = run[q];
                    }
                  }
                });
@@ -404,19 +404,19 @@ struct Walk2Shape {
   }
 };
 
+// The walk of CTA `cta` of one MTTKRP (shared by the single-tensor kernel and
+// the batched one).  smem holds Walk2Shape::smem_bytes(R) bytes; s_row and
+// w_row hold SEGS * 2 and kWalkWarps * 2 entries.
 template <typename T, int VEC, int G>
-__global__ void __launch_bounds__(kWalkWarps * 32, (Walk2Shape<T, VEC, G>::MIN_BLOCKS))
-    mttkrp_walk2(const MttkrpParams a) {
+__device__ __forceinline__ void walk2_cta(const MttkrpParams& a, int cta, float* smem,
+                                          int32_t* s_row, int32_t* w_row) {
   using Shape = Walk2Shape<T, VEC, G>;
   constexpr int NG = Shape::NG, SEGS = Shape::SEGS, U = Shape::U;
   constexpr int NT = kWalkWarps * 32;
-  extern __shared__ __align__(16) float smem[];
   const int R = a.R;
   float* s_val = smem;                           // [SEGS * 2][R]
   float* w_val = smem + (size_t)SEGS * 2 * R;    // [kWalkWarps * 2][R]
   float* vb = w_val + (size_t)kWalkWarps * 2 * R;  // [U][VEC][NT] parked fiber sums
-  __shared__ int32_t s_row[SEGS * 2];
-  __shared__ int32_t w_row[kWalkWarps * 2];
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, (Walk2Shape<T, VEC, G>::MIN_B
   const bool colok = col0 < R;
   const int sl = warp * NG + g;
   const int nnz = (int)a.nnz;
-  const int cta_p0 = (int)min((int64_t)blockIdx.x * SEGS * a.seg, a.nnz);
+  const int cta_p0 = (int)min((int64_t)cta * SEGS * a.seg, a.nnz);
   const int cta_p1 = (int)min((int64_t)cta_p0 + (int64_t)SEGS * a.seg, a.nnz);
   const int p0 = (int)min((int64_t)cta_p0 + (int64_t)sl * a.seg, a.nnz);
   const int p1 = min(p0 + a.seg, nnz);
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, (Walk2Shape<T, VEC, G>::MIN_B
   int q = 0;          // fiber holding the current nonzero
   int row_cur = -1;
   if (active) {
-    q = a.seg_fib[(int64_t)blockIdx.x * SEGS + sl];
+    q = a.seg_fib[(int64_t)cta * SEGS + sl];
     row_cur = a.fiber_row[q];
   }
   bool head_open = true;
@@ -564,8 +564,79 @@ __global__ void __launch_bounds__(kWalkWarps * 32, (Walk2Shape<T, VEC, G>::MIN_B
     put_slot(1, row_cur, acc);
   }
   __syncthreads();
-  mttkrp_merge_cta<SEGS, NG>(a, s_row, s_val, w_row, w_val, lane, warp, cta_p0, cta_p1);
+  mttkrp_merge_cta<SEGS, NG>(a, cta, s_row, s_val, w_row, w_val, lane, warp, cta_p0, cta_p1);
 }
+
+template <typename T, int VEC, int G>
+__global__ void __launch_bounds__(kWalkWarps * 32, (Walk2Shape<T, VEC, G>::MIN_BLOCKS))
+    mttkrp_walk2(const MttkrpParams a) {
+  using Shape = Walk2Shape<T, VEC, G>;
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int32_t s_row[Shape::SEGS * 2];
+  __shared__ int32_t w_row[kWalkWarps * 2];
+  walk2_cta<T, VEC, G>(a, blockIdx.x, smem, s_row, w_row);
+}
+
+// ---------------------------------------------------------------------------
+// Batched MTTKRP: the jobs of a batch that share (R, factor type) form one
+// block-diagonal tensor (a "rank class": indices offset per job, factors
+// pooled), so a class is one walk.  mttkrp_walk2_multi walks up to
+// kMaxClasses classes in one persistent launch: block b takes the virtual CTAs
+// b, b + gridDim.x, ... of the concatenated class ranges, and each class runs
+// the walk shape its autotuned (VEC, G) selects.  The per-class parameters stay
+// in the kernel's parameter space (__grid_constant__).
+// ---------------------------------------------------------------------------
+constexpr int kMaxClasses = 4;
+
+// Walk shapes compiled into the batched kernel: (VEC, G) by id.
+constexpr int kMultiShapes = 6;
+__host__ __device__ constexpr int multi_shape_vec(int id) { return id < 3 ? 4 : 8; }
+__host__ __device__ constexpr int multi_shape_G(int id) {
+  return id == 0 ? 2 : id == 1 ? 4 : id == 2 ? 8 : id == 3 ? 1 : id == 4 ? 2 : 4;
+}
+inline int multi_shape_id(int vec, int G) {
+  for (int i = 0; i < kMultiShapes; ++i)
+    if (multi_shape_vec(i) == vec && multi_shape_G(i) == G) return i;
+  return -1;
+}
+constexpr int kMultiMaxSegs = kWalkWarps * 32;  // SEGS of the G = 1 shape
+
+struct MultiWalkParams {
+  MttkrpParams p[kMaxClasses];
+  int shape[kMaxClasses];          // multi shape id of each class
+  int cta_begin[kMaxClasses + 1];  // virtual CTAs [cta_begin[c], cta_begin[c + 1]) walk class c
+  int nclass;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kWalkWarps * 32, 3)
+    mttkrp_walk2_multi(const __grid_constant__ MultiWalkParams mp) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int32_t s_row[kMultiMaxSegs * 2];
+  __shared__ int32_t w_row[kWalkWarps * 2];
+  const int total = mp.cta_begin[mp.nclass];
+  for (int v = blockIdx.x; v < total; v += gridDim.x) {
+    int c = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxClasses; ++k)
+      if (k < mp.nclass && v >= mp.cta_begin[k]) c = k;
+    const MttkrpParams& a = mp.p[c];
+    const int cta = v - mp.cta_begin[c];
+    __syncthreads();  // the previous virtual CTA's merge is done with shared memory
+    switch (mp.shape[c]) {
+      case 0: walk2_cta<T, multi_shape_vec(0), multi_shape_G(0)>(a, cta, smem, s_row, w_row); break;
+      case 1: walk2_cta<T, multi_shape_vec(1), multi_shape_G(1)>(a, cta, smem, s_row, w_row); break;
+      case 2: walk2_cta<T, multi_shape_vec(2), multi_shape_G(2)>(a, cta, smem, s_row, w_row); break;
+      case 3: walk2_cta<T, multi_shape_vec(3), multi_shape_G(3)>(a, cta, smem, s_row, w_row); break;
+      case 4: walk2_cta<T, multi_shape_vec(4), multi_shape_G(4)>(a, cta, smem, s_row, w_row); break;
+      default: walk2_cta<T, multi_shape_vec(5), multi_shape_G(5)>(a, cta, smem, s_row, w_row); break;
+    }
+  }
+}
+
+// Launch the batched walk (defined in the batch instantiation units).
+template <typename T>
+cudaError_t launch_walk2_multi(const MultiWalkParams& mp, size_t smem, int grid, cudaStream_t s);
 
 // Launchers of the carry fix-up (mttkrp.cu) and of the segment-start search
 // (build.cu), shared with the allocation-free entry point.
@@ -575,6 +646,9 @@ cudaError_t launch_mttkrp_fixup(const int32_t* carry_row, const float* carry,
                                 cudaStream_t s);
 cudaError_t launch_segment_starts(const int64_t* nz_ptr, int64_t nfib, int64_t nseg, int64_t seg,
                                   int32_t* seg_fib, cudaStream_t s);
+// Zero bits[(nnz + 31) / 32] and set the bit of the last nonzero of every fiber.
+cudaError_t launch_fiber_end_bits(const int64_t* nz_ptr, int64_t nfib, int64_t nnz, uint32_t* bits,
+                                  cudaStream_t s);
 
 // Launch one walk configuration (defined in the instantiation units).
 template <typename T>

@@ -52,6 +52,17 @@ class dfacto_csr_view(ctypes.Structure):
                 ("nz_val", ctypes.c_void_p)]
 
 
+class dfacto_batch_options(ctypes.Structure):
+    _fields_ = [("side_streams", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class dfacto_batch_class(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int32), ("factor_dtype", ctypes.c_int32),
+                ("n_jobs", ctypes.c_int32), ("vec", ctypes.c_int32), ("lanes", ctypes.c_int32),
+                ("seg_nnz", ctypes.c_int32), ("nnz", ctypes.c_int64), ("tuned_ms", ctypes.c_double)]
+
+
 _lib = None
 
 # Every symbol the header declares, with its ctypes signature.
@@ -76,6 +87,15 @@ SIGNATURES = {
     "dfacto_fit": (_I, [_P, _P]),
     "dfacto_get_csr": (_I, [_P, _I, _P]),
     "dfacto_mttkrp_noalloc": (_I, [_P, _P, _P, ctypes.c_int32, _P, _P]),
+    "dfacto_batch_options_init": (None, [_P]),
+    "dfacto_batch_create": (_I, [_P, ctypes.c_int32, _P, _P, _P]),
+    "dfacto_batch_destroy": (None, [_P]),
+    "dfacto_batch_mttkrp": (_I, [_P, _I, _P]),
+    "dfacto_batch_als_iter": (_I, [_P, _P]),
+    "dfacto_batch_sync": (_I, [_P]),
+    "dfacto_batch_num_classes": (ctypes.c_int32, [_P]),
+    "dfacto_batch_get_class": (_I, [_P, ctypes.c_int32, _P]),
+    "dfacto_batch_last_error": (ctypes.c_char_p, [_P]),
 }
 
 
@@ -96,10 +116,14 @@ def load(path: str = LIB_PATH):
     return _lib
 
 
-def _check(st: int, h=None, allow=()) -> int:
+def _check(st: int, h=None, allow=(), batch=None) -> int:
     if st == OK or st in allow:
         return st
     msg = load().dfacto_status_str(st).decode()
+    if batch is not None:
+        detail = load().dfacto_batch_last_error(batch)
+        if detail:
+            msg += ": " + detail.decode()
     if h is not None:
         detail = load().dfacto_last_error(h)
         if detail:
@@ -318,3 +342,92 @@ class Tensor:
 
     def csr(self, mode: int) -> dict:
         return csr_to_tensors(dfacto_get_csr(self.h, mode))
+
+
+# ---- batches -----------------------------------------------------------------
+
+def dfacto_batch_options_init(side_streams: int = 0, use_graph: bool = True,
+                              autotune: bool = True) -> dfacto_batch_options:
+    opt = dfacto_batch_options()
+    load().dfacto_batch_options_init(ctypes.byref(opt))
+    if side_streams:
+        opt.side_streams = int(side_streams)
+    opt.use_graph = int(bool(use_graph))
+    opt.autotune = int(bool(autotune))
+    return opt
+
+
+def dfacto_batch_create(handles: Sequence, opt: Optional[dfacto_batch_options] = None, stream=None):
+    arr = (ctypes.c_void_p * len(handles))(*[ctypes.c_void_p(h) for h in handles])
+    out = ctypes.c_void_p()
+    st = load().dfacto_batch_create(arr, len(handles), ctypes.byref(opt) if opt is not None else None,
+                                    _stream_ptr(stream), ctypes.byref(out))
+    _check(st)
+    return out.value
+
+
+def dfacto_batch_destroy(b) -> None:
+    if b:
+        load().dfacto_batch_destroy(b)
+
+
+def dfacto_batch_mttkrp(b, mode: int, outs: Sequence[torch.Tensor]) -> Sequence[torch.Tensor]:
+    for t in outs:
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    arr = (ctypes.c_void_p * len(outs))(*[t.data_ptr() for t in outs])
+    _check(load().dfacto_batch_mttkrp(b, int(mode), arr), batch=b)
+    return outs
+
+
+def dfacto_batch_als_iter(b, n: int, want_fits: bool = True) -> Tuple[int, Optional[List[float]]]:
+    fits = (ctypes.c_double * n)() if want_fits else None
+    st = _check(load().dfacto_batch_als_iter(b, fits), allow=(ESINGULAR,), batch=b)
+    return st, (list(fits) if want_fits else None)
+
+
+def dfacto_batch_sync(b) -> None:
+    _check(load().dfacto_batch_sync(b), batch=b)
+
+
+def dfacto_batch_classes(b) -> List[dfacto_batch_class]:
+    out = []
+    for k in range(load().dfacto_batch_num_classes(b)):
+        c = dfacto_batch_class()
+        _check(load().dfacto_batch_get_class(b, k, ctypes.byref(c)), batch=b)
+        out.append(c)
+    return out
+
+
+class Batch:
+    """Owning wrapper of a batch of Tensor jobs.  Holds references to the jobs
+    so that they outlive the batch (the batch must be destroyed first)."""
+
+    def __init__(self, tensors: Sequence["Tensor"], side_streams: int = 0, use_graph: bool = True,
+                 autotune: bool = True, stream=None):
+        self.tensors = list(tensors)
+        self.opt = dfacto_batch_options_init(side_streams, use_graph, autotune)
+        self.b = dfacto_batch_create([t.h for t in self.tensors], self.opt, stream)
+
+    def close(self) -> None:
+        b = getattr(self, "b", None)
+        if b:
+            dfacto_batch_destroy(b)
+            self.b = None
+
+    def __del__(self):
+        self.close()
+
+    def mttkrp(self, mode: int, outs: Optional[Sequence[torch.Tensor]] = None):
+        if outs is None:
+            outs = [torch.empty(t.dims[mode], t.rank, dtype=torch.float32, device="cuda")
+                    for t in self.tensors]
+        return dfacto_batch_mttkrp(self.b, mode, outs)
+
+    def als_iter(self, want_fits: bool = True):
+        return dfacto_batch_als_iter(self.b, len(self.tensors), want_fits)
+
+    def sync(self) -> None:
+        dfacto_batch_sync(self.b)
+
+    def classes(self) -> List[dfacto_batch_class]:
+        return dfacto_batch_classes(self.b)

@@ -53,6 +53,9 @@ int main(void) {
   printf("%zu %zu %zu %zu\\n", sizeof(dfacto_info), offsetof(dfacto_info, nnz),
          offsetof(dfacto_info, norm_x2), offsetof(dfacto_info, vec));
   printf("%zu %zu\\n", sizeof(dfacto_csr_view), offsetof(dfacto_csr_view, nz_val));
+  printf("%zu %zu\\n", sizeof(dfacto_batch_options), offsetof(dfacto_batch_options, reserved));
+  printf("%zu %zu %zu\\n", sizeof(dfacto_batch_class), offsetof(dfacto_batch_class, nnz),
+         offsetof(dfacto_batch_class, tuned_ms));
   return 0;
 }
 ''')
@@ -64,7 +67,10 @@ int main(void) {
             dfacto.dfacto_options.walk.offset,
             ctypes.sizeof(dfacto.dfacto_info), dfacto.dfacto_info.nnz.offset,
             dfacto.dfacto_info.norm_x2.offset, dfacto.dfacto_info.vec.offset,
-            ctypes.sizeof(dfacto.dfacto_csr_view), dfacto.dfacto_csr_view.nz_val.offset]
+            ctypes.sizeof(dfacto.dfacto_csr_view), dfacto.dfacto_csr_view.nz_val.offset,
+            ctypes.sizeof(dfacto.dfacto_batch_options), dfacto.dfacto_batch_options.reserved.offset,
+            ctypes.sizeof(dfacto.dfacto_batch_class), dfacto.dfacto_batch_class.nnz.offset,
+            dfacto.dfacto_batch_class.tuned_ms.offset]
     assert [int(x) for x in got] == want
 
 
@@ -95,3 +101,24 @@ def test_host_side_argument_checks(lib):
                 "dfacto_fit": (None, None), "dfacto_sync": (None,)}[fn]
         assert getattr(lib, fn)(*args) == dfacto.EINVAL
     assert lib.dfacto_status_str(dfacto.EDUP) == b"duplicate coordinate"
+
+
+def test_batch_host_side_argument_checks(lib):
+    """Batch entry points reject null and out-of-range arguments on the host."""
+    from paper_1406_4519_gb300 import dfacto
+    out = ctypes.c_void_p()
+    assert lib.dfacto_batch_create(None, 1, None, None, ctypes.byref(out)) == dfacto.EINVAL
+    jobs = (ctypes.c_void_p * 1)(None)
+    assert lib.dfacto_batch_create(jobs, 1, None, None, ctypes.byref(out)) == dfacto.EINVAL
+    assert lib.dfacto_batch_create(jobs, 0, None, None, ctypes.byref(out)) == dfacto.EINVAL
+    assert lib.dfacto_batch_create(jobs, 1, None, None, None) == dfacto.EINVAL
+    assert out.value is None
+    assert lib.dfacto_batch_mttkrp(None, 0, None) == dfacto.EINVAL
+    assert lib.dfacto_batch_als_iter(None, None) == dfacto.EINVAL
+    assert lib.dfacto_batch_sync(None) == dfacto.EINVAL
+    assert lib.dfacto_batch_num_classes(None) == 0
+    c = dfacto.dfacto_batch_class()
+    assert lib.dfacto_batch_get_class(None, 0, ctypes.byref(c)) == dfacto.EINVAL
+    lib.dfacto_batch_destroy(None)
+    opt = dfacto.dfacto_batch_options_init()
+    assert (opt.side_streams, opt.use_graph, opt.autotune) == (16, 1, 1)
