@@ -293,21 +293,21 @@ dfacto_status dfacto_mttkrp_noalloc(const dfacto_csr_view* csr, const float* F_i
  * once.  Jobs that share (R, factor type) form a rank class: their flattened
  * CSR copies are concatenated into one block-diagonal tensor (indices offset
  * per job) and their factors are pooled, so the MTTKRP of a mode for every
- * job of every class is one persistent kernel launch.  The per-job R x R
- * steps (Gamma^{-1}, normalisation, Grams, fit) run as parallel branches, and
- * from the second sweep on the whole sweep is replayed as one CUDA graph.
+ * job of every class is one persistent kernel launch.  The per-job steps
+ * (Gamma^{-1}, N Gamma^{-1}, normalisation, Grams, fit) run as one batched
+ * launch per step and rank class, and from the second sweep on the whole
+ * sweep is replayed as one CUDA graph.
  * ------------------------------------------------------------------------ */
 typedef struct dfacto_batch dfacto_batch_t;
 
 typedef struct {
-  int32_t side_streams; /* parallel branches for the per-job steps (0: 16) */
   int32_t use_graph;    /* nonzero: capture the sweep into a CUDA graph and
                            replay it from the second sweep on */
   int32_t autotune;     /* nonzero: time walk shapes per rank class at creation */
-  int32_t reserved[5];  /* zero */
+  int32_t reserved[6];  /* zero */
 } dfacto_batch_options;
 
-/* Defaults: 16 side streams, graph on, autotune on. */
+/* Defaults: graph on, autotune on. */
 void dfacto_batch_options_init(dfacto_batch_options* opt);
 
 /*
@@ -321,9 +321,9 @@ void dfacto_batch_options_init(dfacto_batch_options* opt);
  *           leaves the batch unusable (its calls return DFACTO_EINVAL).
  *   n       1..65536.
  *   opt     options, or NULL for the defaults.
- *   stream  cudaStream_t the batch's work is ordered after and that
- *           dfacto_batch_sync waits for (NULL: the legacy default stream).
- *           The batch forks its own non-blocking streams from it.
+ *   stream  cudaStream_t the batch's calls are ordered after, and that waits
+ *           for each call's work (NULL: the legacy default stream).  The batch
+ *           runs on two non-blocking streams of its own.
  * The batch owns a second copy of every job's CSR arrays (concatenated per
  * rank class) and one MTTKRP output buffer per class and mode.  Returns
  * DFACTO_EINVAL for bad arguments, DFACTO_ENOMEM, DFACTO_ECUDA.  Synchronous.

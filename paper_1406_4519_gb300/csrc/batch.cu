@@ -10,8 +10,9 @@
 // j's factors and writes rows of job j's output.  The walk of every class of
 // one factor type runs in one persistent launch (mttkrp_walk2_multi).
 //
-// The R x R steps of Algorithm 2 stay per job (their sizes differ), issued on
-// parallel streams; from the second sweep on the whole sweep is one CUDA graph.
+// The R x R and row steps of Algorithm 2 run once per rank class as batched
+// launches (each block finds its job and runs that job's step); from the
+// second sweep on the whole sweep is one CUDA graph.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -25,7 +26,6 @@ struct dfacto_batch;
 namespace dfacto {
 namespace {
 
-constexpr int kMaxSideStreams = 64;
 constexpr int kTuneSegs[] = {64, 128, 256};
 
 __global__ void copy_add_i32(const int32_t* __restrict__ src, int64_t n, int32_t add,
@@ -108,6 +108,10 @@ struct BatchClass {
   int32_t* carry_row = nullptr;    // [carry_cap x 2]
   int64_t carry_cap = 0;           // CTAs
   double tuned_ms = 0.0;
+  DenseJob* dense[3] = {nullptr, nullptr, nullptr};  // device [jobs] per mode
+  int32_t* begin[3] = {nullptr, nullptr, nullptr};   // device [jobs + 1] first row block
+  int total_blocks[3] = {0, 0, 0};
+  std::vector<int> nb[3];                            // row blocks per job and mode
 
   int segs() const { return kWalkWarps * (32 / cfg.G); }
   int64_t ncta() const {
@@ -126,8 +130,8 @@ struct dfacto_batch {
   std::vector<dfacto::BatchClass> cls;
   cudaStream_t user = nullptr;   // the caller's stream
   cudaStream_t main = nullptr;
-  std::vector<cudaStream_t> side;
-  std::vector<cudaEvent_t> side_ev;
+  cudaStream_t side = nullptr;   // Gamma^{-1} of the next mode, beside the MTTKRP
+  cudaEvent_t side_ev = nullptr;
   cudaEvent_t fork_ev = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -402,64 +406,103 @@ dfacto_status autotune_class(dfacto_batch* b, int k) {
 
 // ---- the sweep ---------------------------------------------------------------
 
-dfacto_status fork(dfacto_batch* b) {
-  DB_CUDA(b, cudaEventRecord(b->fork_ev, b->main));
-  for (cudaStream_t s : b->side) DB_CUDA(b, cudaStreamWaitEvent(s, b->fork_ev, 0));
-  return DFACTO_OK;
-}
-
-dfacto_status join(dfacto_batch* b) {
-  for (size_t i = 0; i < b->side.size(); ++i) {
-    DB_CUDA(b, cudaEventRecord(b->side_ev[i], b->side[i]));
-    DB_CUDA(b, cudaStreamWaitEvent(b->main, b->side_ev[i], 0));
+// Per-job pointers of every class and mode for the batched dense kernels.
+dfacto_status build_dense_tables(dfacto_batch* b) {
+  for (BatchClass& C : b->cls) {
+    const int n = (int)C.jobs.size();
+    for (int mode = 0; mode < 3; ++mode) {
+      const int in = (mode + 1) % 3, f = (mode + 2) % 3;
+      std::vector<DenseJob> tab(n);
+      std::vector<int32_t> begin(n + 1, 0);
+      C.nb[mode].assign(n, 0);
+      for (int t = 0; t < n; ++t) {
+        dfacto_t* h = b->jobs[C.jobs[t]];
+        DenseJob& J = tab[t];
+        J.Gf = h->gram[f];
+        J.Gi = h->gram[in];
+        J.lambda_reg = h->lambda_reg;
+        J.W = h->W;
+        J.W32 = h->W32;
+        J.singular = h->flags + kFlagSingular;
+        J.rr_work = h->rr_work;
+        J.N = C.m[mode].N + (size_t)C.off[mode][t] * C.R;
+        J.rows = h->dims[mode];
+        J.nb = dense_row_blocks(J.rows, C.R);
+        J.Fh = h->Fh;
+        J.partials = h->partials;
+        J.lambda = h->lambda;
+        J.inv_lambda = h->inv_lambda;
+        J.F = h->F[mode];
+        J.gram_out = h->gram[mode];
+        J.ipart = h->ipart;
+        J.GA = h->gram[0];
+        J.GB = h->gram[1];
+        J.GC = h->gram[2];
+        J.scal = h->scal;
+        C.nb[mode][t] = J.nb;
+        begin[t + 1] = begin[t] + J.nb;
+      }
+      C.total_blocks[mode] = begin[n];
+      dfacto_status st;
+      if ((st = balloc(b, &C.dense[mode], sizeof(DenseJob) * (size_t)n)) != DFACTO_OK) return st;
+      if ((st = balloc(b, &C.begin[mode], sizeof(int32_t) * (size_t)(n + 1))) != DFACTO_OK) return st;
+      DB_CUDA(b, cudaMemcpy(C.dense[mode], tab.data(), sizeof(DenseJob) * (size_t)n, cudaMemcpyHostToDevice));
+      DB_CUDA(b, cudaMemcpy(C.begin[mode], begin.data(), sizeof(int32_t) * (size_t)(n + 1),
+                            cudaMemcpyHostToDevice));
+    }
   }
   return DFACTO_OK;
 }
 
-// Issue one ALS sweep of every job plus its fit, ending on b->main.
+// Issue one ALS sweep of every job plus its fit, ending on b->main.  Per mode:
+// Gamma^{-1} of every job (side stream) beside the MTTKRP of every class
+// (main), then N Gamma^{-1}, normalisation, store and Gram, one launch per step
+// and rank class.
 dfacto_status issue_sweep(dfacto_batch* b) {
   const int n = (int)b->jobs.size();
-  const int S = (int)b->side.size();
-  std::vector<cudaStream_t> saved(n);
-  for (int j = 0; j < n; ++j) saved[j] = b->jobs[j]->stream;
-  auto restore = [&]() {
-    for (int j = 0; j < n; ++j) b->jobs[j]->stream = saved[j];
-  };
-  auto job_err = [&](int j, dfacto_status st) {
-    b->err = "job " + std::to_string(j) + ": " + b->jobs[j]->err;
-    return st;
-  };
   zero_job_flags<<<grid_of((int64_t)n * kNumFlags), 256, 0, b->main>>>(b->d_flags, n);
   DF_COUNT();
-  dfacto_status st = DFACTO_OK;
-  for (int mode = 0; mode < 3 && st == DFACTO_OK; ++mode) {
-    if ((st = fork(b)) != DFACTO_OK) break;
-    for (int j = 0; j < n && st == DFACTO_OK; ++j) {
-      b->jobs[j]->stream = b->side[j % S];
-      if ((st = als_pre(b->jobs[j], mode)) != DFACTO_OK) st = job_err(j, st);
+  // Grams of factors set from outside the batch (only before the graph exists).
+  for (int j = 0; j < n; ++j) {
+    dfacto_t* h = b->jobs[j];
+    bool missing = false;
+    for (int m = 0; m < 3; ++m) missing = missing || !h->gram_valid[m];
+    if (!missing) continue;
+    cudaStream_t saved = h->stream;
+    h->stream = b->main;
+    dfacto_status st = DFACTO_OK;
+    for (int m = 0; m < 3 && st == DFACTO_OK; ++m)
+      if (!h->gram_valid[m]) st = gram_of_factor(h, m);
+    h->stream = saved;
+    if (st != DFACTO_OK) {
+      b->err = "job " + std::to_string(j) + ": " + h->err;
+      return st;
     }
-    if (st != DFACTO_OK) break;
-    if ((st = batch_mttkrp_issue(b, mode, b->main, {})) != DFACTO_OK) break;
-    if ((st = fork(b)) != DFACTO_OK) break;
-    for (size_t k = 0; k < b->cls.size() && st == DFACTO_OK; ++k) {
-      const BatchClass& C = b->cls[k];
-      for (size_t t = 0; t < C.jobs.size() && st == DFACTO_OK; ++t) {
-        const int j = C.jobs[t];
-        b->jobs[j]->stream = b->side[j % S];
-        float* N = C.m[mode].N + (size_t)C.off[mode][t] * C.R;
-        if ((st = als_post(b->jobs[j], mode, N)) != DFACTO_OK) st = job_err(j, st);
+  }
+  for (int mode = 0; mode < 3; ++mode) {
+    DB_CUDA(b, cudaEventRecord(b->fork_ev, b->main));
+    DB_CUDA(b, cudaStreamWaitEvent(b->side, b->fork_ev, 0));
+    for (const BatchClass& C : b->cls)
+      DB_CUDA(b, batch_gamma_inverse(C.dense[mode], (int)C.jobs.size(), C.R, b->side));
+    dfacto_status st = batch_mttkrp_issue(b, mode, b->main, {});
+    if (st != DFACTO_OK) {
+      cudaEventRecord(b->side_ev, b->side);  // rejoin before returning
+      cudaStreamWaitEvent(b->main, b->side_ev, 0);
+      return st;
+    }
+    DB_CUDA(b, cudaEventRecord(b->side_ev, b->side));
+    DB_CUDA(b, cudaStreamWaitEvent(b->main, b->side_ev, 0));
+    for (BatchClass& C : b->cls) {
+      DB_CUDA(b, batch_als_post(C.dense[mode], C.begin[mode], (int)C.jobs.size(), C.total_blocks[mode],
+                                C.R, C.dtype, mode == 2, b->main));
+      for (size_t t = 0; t < C.jobs.size(); ++t) {
+        dfacto_t* h = b->jobs[C.jobs[t]];
+        h->gram_valid[mode] = true;
+        if (mode == 2) h->ipart_blocks = C.nb[2][t];
       }
     }
-    if (st == DFACTO_OK) st = join(b);
   }
-  if (st == DFACTO_OK) st = fork(b);
-  for (int j = 0; j < n && st == DFACTO_OK; ++j) {
-    b->jobs[j]->stream = b->side[j % S];
-    if ((st = als_fit(b->jobs[j])) != DFACTO_OK) st = job_err(j, st);
-  }
-  if (st == DFACTO_OK) st = join(b);
-  restore();
-  if (st != DFACTO_OK) return st;
+  for (const BatchClass& C : b->cls) DB_CUDA(b, batch_fit(C.dense[2], (int)C.jobs.size(), C.R, b->main));
   gather_results<<<grid_of(n), 256, 0, b->main>>>(b->d_scal, b->d_flags, n, b->d_bad, b->d_fits,
                                                   b->d_status);
   DF_COUNT();
@@ -488,10 +531,10 @@ void release(dfacto_batch* b) {
   for (void* p : b->owned) cudaFree(p);
   b->owned.clear();
   drop_graph(b);
-  for (cudaStream_t s : b->side) cudaStreamDestroy(s);
-  for (cudaEvent_t e : b->side_ev) cudaEventDestroy(e);
-  b->side.clear();
-  b->side_ev.clear();
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->side_ev) cudaEventDestroy(b->side_ev);
+  b->side = nullptr;
+  b->side_ev = nullptr;
   if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   if (b->main) cudaStreamDestroy(b->main);
   if (b->h_fits) cudaFreeHost(b->h_fits);
@@ -542,7 +585,6 @@ extern "C" {
 void dfacto_batch_options_init(dfacto_batch_options* opt) {
   if (!opt) return;
   std::memset(opt, 0, sizeof(*opt));
-  opt->side_streams = 16;
   opt->use_graph = 1;
   opt->autotune = 1;
 }
@@ -555,8 +597,6 @@ dfacto_status dfacto_batch_create(dfacto_t* const* jobs, int32_t n, const dfacto
   dfacto_batch_options opt;
   if (opt_in) opt = *opt_in;
   else dfacto_batch_options_init(&opt);
-  if (opt.side_streams == 0) opt.side_streams = 16;
-  if (opt.side_streams < 1 || opt.side_streams > kMaxSideStreams) return DFACTO_EINVAL;
   for (int j = 0; j < n; ++j)
     if (!jobs[j] || jobs[j]->batch) return DFACTO_EINVAL;
   {
@@ -581,16 +621,10 @@ dfacto_status dfacto_batch_create(dfacto_t* const* jobs, int32_t n, const dfacto
     return st;
   };
   if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+      cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->side_ev, cudaEventDisableTiming) != cudaSuccess)
     return bail(DFACTO_ECUDA);
-  for (int i = 0; i < opt.side_streams; ++i) {
-    cudaStream_t s;
-    cudaEvent_t e;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return bail(DFACTO_ECUDA);
-    b->side.push_back(s);
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bail(DFACTO_ECUDA);
-    b->side_ev.push_back(e);
-  }
   for (dfacto_t* h : b->jobs)
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(DFACTO_ECUDA);
 
@@ -692,6 +726,10 @@ dfacto_status dfacto_batch_create(dfacto_t* const* jobs, int32_t n, const dfacto
       }
       h->batch = b;
     }
+  }
+  if ((st = build_dense_tables(b)) != DFACTO_OK) {
+    unpool(b);
+    return bail(st);
   }
   if (opt.autotune) {
     for (int k = 0; k < (int)b->cls.size(); ++k)

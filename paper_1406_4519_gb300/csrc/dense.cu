@@ -32,17 +32,19 @@ constexpr int kT = 256;          // threads of the row-pass and Gram kernels
 constexpr int kTile = 64;        // rows per staged tile
 constexpr int kFoldTiles = 8;    // tiles summed in FP32 before folding into FP64
 constexpr int kMaxBlocks = 152 * 4;
-constexpr int kMaxR = 128;
 
 unsigned row_blocks(int64_t rows) {
   const int64_t b = (rows + 4 * kTile - 1) / (4 * kTile);
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, kMaxBlocks));
 }
 
-// Rows [r0, r1) of the block's share of `rows` (contiguous chunks).
-__device__ __forceinline__ void block_rows(int64_t rows, int64_t& r0, int64_t& r1) {
-  const int64_t chunk = (rows + gridDim.x - 1) / gridDim.x;
-  r0 = min(rows, (int64_t)blockIdx.x * chunk);
+// Rows [r0, r1) of block vb's share of `rows` (contiguous chunks over vgrid
+// blocks).  Kernels take (vb, vgrid) = (blockIdx.x, gridDim.x) when launched
+// for one tensor, or a block's position inside its job when launched for a
+// batch of jobs.
+__device__ __forceinline__ void block_rows(int64_t rows, int vb, int vgrid, int64_t& r0, int64_t& r1) {
+  const int64_t chunk = (rows + vgrid - 1) / vgrid;
+  r0 = min(rows, (int64_t)vb * chunk);
   r1 = min(rows, r0 + chunk);
 }
 
@@ -52,12 +54,12 @@ __device__ __forceinline__ void block_rows(int64_t rows, int64_t& r0, int64_t& r
 // Block x takes 32 entries (one per lane); its eight warps take blocks
 // b = w, w + 8, ... in order; the warp sums are added in warp order.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kT) reduce_partials(const double* __restrict__ part, int nb, int n,
-                                                      int R, bool symmetrize,
-                                                      double* __restrict__ out) {
+__device__ __forceinline__ void reduce_partials_body(const double* __restrict__ part, int nb, int n,
+                                                     int R, bool symmetrize, double* __restrict__ out,
+                                                     int vb) {
   __shared__ double s[kT / 32][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int e = blockIdx.x * 32 + lane;
+  const int e = vb * 32 + lane;
   double acc = 0.0;
   if (e < n) {
     const int et = symmetrize ? (e % R) * R + e / R : e;
@@ -74,6 +76,12 @@ __global__ void __launch_bounds__(kT) reduce_partials(const double* __restrict__
     for (int w = 0; w < kT / 32; ++w) t += s[w][lane];
     out[e] = t;
   }
+}
+
+__global__ void __launch_bounds__(kT) reduce_partials(const double* __restrict__ part, int nb, int n,
+                                                      int R, bool symmetrize,
+                                                      double* __restrict__ out) {
+  reduce_partials_body(part, nb, n, R, symmetrize, out, blockIdx.x);
 }
 
 // Sum of the kT per-thread values v into thread 0 in a fixed order.
@@ -145,7 +153,7 @@ __global__ void __launch_bounds__(kT) gram_tiles(const TX* __restrict__ X, const
 #pragma unroll
     for (int q = 0; q < 16; ++q) { acc[b][q] = 0.0; a32[b][q] = 0.f; }
   int64_t r0, r1;
-  block_rows(rows, r0, r1);
+  block_rows(rows, blockIdx.x, gridDim.x, r0, r1);
   int tiles = 0;
   for (int64_t t0 = r0; t0 < r1; t0 += kTile) {
     const int nt = (int)min((int64_t)kTile, r1 - t0);
@@ -208,12 +216,12 @@ __global__ void __launch_bounds__(kT) gram_tiles(const TX* __restrict__ X, const
 // Loan, Sec. 8.5) gives the pseudo-inverse with cutoff R * eps * max |w|.
 // The (2R^2 + R)-double workspace is shared memory when it fits, else global.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) gamma_inverse(const double* __restrict__ Gf,
-                                                    const double* __restrict__ Gi, int R,
-                                                    double lambda_reg, double* __restrict__ W,
-                                                    float* __restrict__ W32,
-                                                    int32_t* __restrict__ singular,
-                                                    double* __restrict__ gwork, bool in_smem) {
+__device__ __forceinline__ void gamma_inverse_body(const double* __restrict__ Gf,
+                                                   const double* __restrict__ Gi, int R,
+                                                   double lambda_reg, double* __restrict__ W,
+                                                   float* __restrict__ W32,
+                                                   int32_t* __restrict__ singular,
+                                                   double* __restrict__ gwork, bool in_smem) {
   extern __shared__ double swork[];
   double* work = in_smem ? swork : gwork;
   double* A = work;               // [R][R] working copy / L
@@ -350,6 +358,15 @@ __global__ void __launch_bounds__(256) gamma_inverse(const double* __restrict__ 
   }
 }
 
+__global__ void __launch_bounds__(256) gamma_inverse(const double* __restrict__ Gf,
+                                                    const double* __restrict__ Gi, int R,
+                                                    double lambda_reg, double* __restrict__ W,
+                                                    float* __restrict__ W32,
+                                                    int32_t* __restrict__ singular,
+                                                    double* __restrict__ gwork, bool in_smem) {
+  gamma_inverse_body(Gf, Gi, R, lambda_reg, W, W32, singular, gwork, in_smem);
+}
+
 // ---------------------------------------------------------------------------
 // Row passes.  A block takes a contiguous chunk of rows in tiles of kTile; the
 // tile of the input rows is staged (row stride R + 1) and thread t computes
@@ -381,10 +398,10 @@ __device__ __forceinline__ void stage_rr(const float* __restrict__ M, int R, int
 
 // ALS pass A: Fh = N W (W = Gamma^{-1}) and per-block column sums of squares
 // of Fh, colsq[block][R].
-__global__ void __launch_bounds__(kT) als_solve_rows(const float* __restrict__ N,
-                                                     const float* __restrict__ W32, int64_t rows,
-                                                     int R, float* __restrict__ Fh,
-                                                     double* __restrict__ colsq) {
+__device__ __forceinline__ void als_solve_rows_body(const float* __restrict__ N,
+                                                    const float* __restrict__ W32, int64_t rows,
+                                                    int R, float* __restrict__ Fh,
+                                                    double* __restrict__ colsq, int vb, int vgrid) {
   extern __shared__ __align__(16) float sm[];
   const int R4 = (R + 3) / 4, W = 4 * R4;
   float* S = sm;                        // [R][W]
@@ -396,7 +413,7 @@ __global__ void __launch_bounds__(kT) als_solve_rows(const float* __restrict__ N
   const bool active = rsub < rstep;
   double sq[4] = {0.0, 0.0, 0.0, 0.0};
   int64_t r0, r1;
-  block_rows(rows, r0, r1);
+  block_rows(rows, vb, vgrid, r0, r1);
   for (int64_t t0 = r0; t0 < r1; t0 += kTile) {
     const int nt = (int)min((int64_t)kTile, r1 - t0);
     __syncthreads();
@@ -424,17 +441,23 @@ __global__ void __launch_bounds__(kT) als_solve_rows(const float* __restrict__ N
   for (int c = 0; c < R; ++c) {
     const double v = (active && cg == c / 4) ? sq[c % 4] : 0.0;
     const double t = block_sum(v, red);
-    if (threadIdx.x == 0) colsq[(size_t)blockIdx.x * R + c] = t;
+    if (threadIdx.x == 0) colsq[(size_t)vb * R + c] = t;
   }
+}
+
+__global__ void __launch_bounds__(kT) als_solve_rows(const float* __restrict__ N,
+                                                     const float* __restrict__ W32, int64_t rows,
+                                                     int R, float* __restrict__ Fh,
+                                                     double* __restrict__ colsq) {
+  als_solve_rows_body(N, W32, rows, R, Fh, colsq, blockIdx.x, gridDim.x);
 }
 
 // lambda[r] = sqrt(sum_b colsq[b][r]); inv[r] = 1/lambda (1 where lambda = 0).
 // One block per column.
-__global__ void __launch_bounds__(kT) finish_lambda(const double* __restrict__ colsq, int nb, int R,
-                                                    double* __restrict__ lambda,
-                                                    float* __restrict__ inv) {
+__device__ __forceinline__ void finish_lambda_body(const double* __restrict__ colsq, int nb, int R,
+                                                   double* __restrict__ lambda,
+                                                   float* __restrict__ inv, int r) {
   __shared__ double red[kT];
-  const int r = blockIdx.x;
   double v = 0.0;
   for (int b = threadIdx.x; b < nb; b += kT) v += colsq[(size_t)b * R + r];
   const double t = block_sum(v, red);
@@ -445,17 +468,23 @@ __global__ void __launch_bounds__(kT) finish_lambda(const double* __restrict__ c
   }
 }
 
+__global__ void __launch_bounds__(kT) finish_lambda(const double* __restrict__ colsq, int nb, int R,
+                                                    double* __restrict__ lambda,
+                                                    float* __restrict__ inv) {
+  finish_lambda_body(colsq, nb, R, lambda, inv, blockIdx.x);
+}
+
 // ALS pass B: F = Fh / lambda stored in T; Gram partials of the stored values
 // gpart[block][R*R]; with N != null also the scalar partial
 // sum_{o,r} lambda_r F_stored[o,r] N[o,r] (= <X, Xhat> after the mode-3 update).
 template <typename T, int BPT>
-__global__ void __launch_bounds__(kT) als_store_rows(const float* __restrict__ Fh,
-                                                     const float* __restrict__ inv,
-                                                     const double* __restrict__ lambda,
-                                                     int64_t rows, int R, T* __restrict__ F,
-                                                     double* __restrict__ gpart,
-                                                     const float* __restrict__ N,
-                                                     double* __restrict__ ipart) {
+__device__ __forceinline__ void als_store_rows_body(const float* __restrict__ Fh,
+                                                    const float* __restrict__ inv,
+                                                    const double* __restrict__ lambda,
+                                                    int64_t rows, int R, T* __restrict__ F,
+                                                    double* __restrict__ gpart,
+                                                    const float* __restrict__ N,
+                                                    double* __restrict__ ipart, int vb, int vgrid) {
   extern __shared__ __align__(16) float sm[];
   const int R4 = (R + 3) / 4, W = 4 * R4;
   float* tile = sm;  // [kTile][W] stored values, zero-padded
@@ -473,7 +502,7 @@ __global__ void __launch_bounds__(kT) als_store_rows(const float* __restrict__ F
   int tiles = 0;
   double ip = 0.0;
   int64_t r0, r1;
-  block_rows(rows, r0, r1);
+  block_rows(rows, vb, vgrid, r0, r1);
   for (int64_t t0 = r0; t0 < r1; t0 += kTile) {
     const int nt = (int)min((int64_t)kTile, r1 - t0);
     __syncthreads();
@@ -537,7 +566,7 @@ __global__ void __launch_bounds__(kT) als_store_rows(const float* __restrict__ F
   }
   if (N) {
     const double t = block_sum(ip, red);
-    if (threadIdx.x == 0) ipart[blockIdx.x] = t;
+    if (threadIdx.x == 0) ipart[vb] = t;
   }
   __syncthreads();
   double* rsm = reinterpret_cast<double*>(sm);  // [kT][16] over the tile space
@@ -555,21 +584,32 @@ __global__ void __launch_bounds__(kT) als_store_rows(const float* __restrict__ F
         for (int gg = 0; gg < ngrp; ++gg)
           t += rsm[(gg * nblk + (nblk <= kT ? blk : (int)threadIdx.x)) * 16 + q];
         const int a = 4 * bi + q / 4, c = 4 * bj + q % 4;
-        if (a < R && c < R) gpart[(size_t)blockIdx.x * R * R + a * R + c] = t;
+        if (a < R && c < R) gpart[(size_t)vb * R * R + a * R + c] = t;
       }
     }
     __syncthreads();
   }
 }
 
+template <typename T, int BPT>
+__global__ void __launch_bounds__(kT) als_store_rows(const float* __restrict__ Fh,
+                                                     const float* __restrict__ inv,
+                                                     const double* __restrict__ lambda,
+                                                     int64_t rows, int R, T* __restrict__ F,
+                                                     double* __restrict__ gpart,
+                                                     const float* __restrict__ N,
+                                                     double* __restrict__ ipart) {
+  als_store_rows_body<T, BPT>(Fh, inv, lambda, rows, R, F, gpart, N, ipart, blockIdx.x, gridDim.x);
+}
+
 // Fit from scalars and Grams (one block):
 //   <X,Xhat> = sum of ipart;  ||Xhat||^2 = lambda^T (GA*GB*GC) lambda.
-__global__ void __launch_bounds__(kT) fit_from_parts(const double* __restrict__ ipart, int nb, int R,
-                                                     const double* __restrict__ lambda,
-                                                     const double* __restrict__ GA,
-                                                     const double* __restrict__ GB,
-                                                     const double* __restrict__ GC,
-                                                     double* __restrict__ scal) {
+__device__ __forceinline__ void fit_from_parts_body(const double* __restrict__ ipart, int nb, int R,
+                                                    const double* __restrict__ lambda,
+                                                    const double* __restrict__ GA,
+                                                    const double* __restrict__ GB,
+                                                    const double* __restrict__ GC,
+                                                    double* __restrict__ scal) {
   __shared__ double red[kT];
   double v = 0.0;
   for (int b = threadIdx.x; b < nb; b += kT) v += ipart[b];
@@ -590,6 +630,15 @@ __global__ void __launch_bounds__(kT) fit_from_parts(const double* __restrict__ 
   }
 }
 
+__global__ void __launch_bounds__(kT) fit_from_parts(const double* __restrict__ ipart, int nb, int R,
+                                                     const double* __restrict__ lambda,
+                                                     const double* __restrict__ GA,
+                                                     const double* __restrict__ GB,
+                                                     const double* __restrict__ GC,
+                                                     double* __restrict__ scal) {
+  fit_from_parts_body(ipart, nb, R, lambda, GA, GB, GC, scal);
+}
+
 // <N, lambda-scaled F> partials for a fit without an ALS sweep.
 template <typename T>
 __global__ void __launch_bounds__(kT) rows_inner(const float* __restrict__ N, const T* __restrict__ F,
@@ -597,7 +646,7 @@ __global__ void __launch_bounds__(kT) rows_inner(const float* __restrict__ N, co
                                                  int R, double* __restrict__ ipart) {
   __shared__ double red[kT];
   int64_t r0, r1;
-  block_rows(rows, r0, r1);
+  block_rows(rows, blockIdx.x, gridDim.x, r0, r1);
   double acc = 0.0;
   float a32 = 0.f;
   int since = 0;
@@ -638,7 +687,7 @@ __global__ void __launch_bounds__(kT) gd_gradient_rows(const float* __restrict__
   const bool active = rsub < rstep;
   double ad[3] = {0.0, 0.0, 0.0};
   int64_t r0, r1;
-  block_rows(rows, r0, r1);
+  block_rows(rows, blockIdx.x, gridDim.x, r0, r1);
   for (int64_t t0 = r0; t0 < r1; t0 += kTile) {
     const int nt = (int)min((int64_t)kTile, r1 - t0);
     __syncthreads();
@@ -796,7 +845,317 @@ __global__ void gd_update(T* __restrict__ F, const float* __restrict__ grad, int
     st_elem(F + t, ld_elem(F + t) - a * grad[t]);
 }
 
+// ---------------------------------------------------------------------------
+// Row passes for R <= 32, one thread per row.  Pass 1 (colnorm_rows) computes
+// the column sums of squares of N Gamma^{-1} without storing it; pass 2
+// (scale_store_rows) recomputes N Gamma^{-1} row by row (same arithmetic, same
+// order, so the same values), scales by 1/lambda, stores F, and forms the Gram
+// of the stored values (and the fit's inner product on the last mode).  Each
+// pass reads N once: 4R + s R bytes per row over both passes instead of a
+// write and a read of N Gamma^{-1} in between.  Gamma^{-1} sits in shared
+// memory as RT x RT (zero-padded), read by broadcast.
+// ---------------------------------------------------------------------------
+constexpr int kPassRowsPerBlock = 1024;
+
+int pass_blocks(int64_t rows) {
+  const int64_t b = (rows + kPassRowsPerBlock - 1) / kPassRowsPerBlock;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, kMaxBlocks));
+}
+
+// Row r of N (R columns) zero-padded to RT.
+template <int RT>
+__device__ __forceinline__ void load_row(const float* __restrict__ N, int64_t r, int R, float (&n)[RT]) {
+  const float* p = N + r * R;
+  if ((R & 3) == 0) {
+#pragma unroll
+    for (int c4 = 0; c4 < RT / 4; ++c4) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (4 * c4 < R) v = __ldg(reinterpret_cast<const float4*>(p) + c4);
+      n[4 * c4] = v.x; n[4 * c4 + 1] = v.y; n[4 * c4 + 2] = v.z; n[4 * c4 + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < RT; ++c) n[c] = c < R ? __ldg(p + c) : 0.f;
+  }
+}
+
+// Columns [c0, c0 + CW) of o = n W (W: RT x RT in shared memory, row k holds
+// the coefficients of n[k]); k ascends, so every caller gets the same values.
+template <int RT, int CW>
+__device__ __forceinline__ void row_solve(const float (&n)[RT], const float* __restrict__ Ws, int c0,
+                                          float (&o)[CW]) {
+#pragma unroll
+  for (int c = 0; c < CW; ++c) o[c] = 0.f;
+#pragma unroll
+  for (int k = 0; k < RT; ++k) {
+    const float a = n[k];
+#pragma unroll
+    for (int c4 = 0; c4 < CW / 4; ++c4) {
+      const float4 w = reinterpret_cast<const float4*>(Ws + k * RT + c0)[c4];
+      o[4 * c4] = fmaf(a, w.x, o[4 * c4]);
+      o[4 * c4 + 1] = fmaf(a, w.y, o[4 * c4 + 1]);
+      o[4 * c4 + 2] = fmaf(a, w.z, o[4 * c4 + 2]);
+      o[4 * c4 + 3] = fmaf(a, w.w, o[4 * c4 + 3]);
+    }
+  }
+}
+
+template <int RT>
+__device__ __forceinline__ void stage_w(const float* __restrict__ W32, int R, float* Ws) {
+  for (int e = threadIdx.x; e < RT * RT; e += kT) {
+    const int k = e / RT, c = e % RT;
+    Ws[e] = (k < R && c < R) ? W32[k * R + c] : 0.f;
+  }
+}
+
+// Output columns are produced CW = min(RT, 16) at a time (fewer live registers).
+template <int RT>
+struct PassShape {
+  static constexpr int CW = RT < 16 ? RT : 16;
+  static constexpr int LD = RT + 4;  // tile row stride (16-byte aligned rows)
+  static constexpr int NB4 = RT / 4, NBLK = NB4 * NB4, NGRP = kT / NBLK;
+};
+
+// Pass 1: colsq[vb][c] = sum over the block's rows of (N W)[row, c]^2.  Each
+// thread sums its rows in FP32; the block adds the threads in FP64, in thread
+// order.
+template <int RT>
+__device__ __forceinline__ void colnorm_rows_body(const float* __restrict__ N,
+                                                  const float* __restrict__ W32, int64_t rows, int R,
+                                                  double* __restrict__ colsq, int vb, int vgrid) {
+  constexpr int CW = PassShape<RT>::CW;
+  __shared__ __align__(16) float Ws[RT * RT];
+  __shared__ float red[kT * (RT + 1)];
+  stage_w<RT>(W32, R, Ws);
+  __syncthreads();
+  int64_t r0, r1;
+  block_rows(rows, vb, vgrid, r0, r1);
+  float sq[RT];
+#pragma unroll
+  for (int c = 0; c < RT; ++c) sq[c] = 0.f;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += kT) {
+    float n[RT];
+    load_row<RT>(N, r, R, n);
+#pragma unroll
+    for (int h = 0; h < RT / CW; ++h) {
+      float o[CW];
+      row_solve<RT, CW>(n, Ws, h * CW, o);
+#pragma unroll
+      for (int c = 0; c < CW; ++c) sq[h * CW + c] = fmaf(o[c], o[c], sq[h * CW + c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < RT; ++c) red[threadIdx.x * (RT + 1) + c] = sq[c];
+  __syncthreads();
+  for (int c = threadIdx.x; c < R; c += kT) {
+    double t = 0.0;
+    for (int i = 0; i < kT; ++i) t += (double)red[i * (RT + 1) + c];
+    colsq[(size_t)vb * R + c] = t;
+  }
+}
+
+// Pass 2: F[row] = (N W)[row] * inv stored in T; Gram partials of the stored
+// values gpart[vb][R*R]: a tile of kT rows at a time goes through shared
+// memory and thread (grp, blk) adds the outer products of the 4 x 4 block blk
+// over rows grp, grp + NGRP, ... in FP32; the groups are added in FP64, in
+// group order.  With with_ip also ipart[vb] = sum lambda_c F_stored[row, c]
+// N[row, c] (the fit's inner product after the last mode).
+template <typename T, int RT>
+__device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ N,
+                                                      const float* __restrict__ W32,
+                                                      const float* __restrict__ inv,
+                                                      const double* __restrict__ lambda, int64_t rows,
+                                                      int R, T* __restrict__ F,
+                                                      double* __restrict__ gpart, bool with_ip,
+                                                      double* __restrict__ ipart, int vb, int vgrid) {
+  using PS = PassShape<RT>;
+  constexpr int CW = PS::CW, LD = PS::LD, NB4 = PS::NB4, NBLK = PS::NBLK, NGRP = PS::NGRP;
+  __shared__ __align__(16) float Ws[RT * RT];
+  __shared__ __align__(16) float tile[kT * LD];
+  __shared__ float s_sc[RT], s_lm[RT];
+  __shared__ double red[kT];
+  stage_w<RT>(W32, R, Ws);
+  for (int c = threadIdx.x; c < RT; c += kT) {
+    s_sc[c] = c < R ? inv[c] : 0.f;
+    s_lm[c] = (with_ip && c < R) ? (float)lambda[c] : 0.f;
+  }
+  const int blk = threadIdx.x % NBLK, grp = threadIdx.x / NBLK;
+  const int bi = blk / NB4, bj = blk % NB4;
+  float a32[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) a32[q] = 0.f;
+  double ip = 0.0;
+  int64_t r0, r1;
+  block_rows(rows, vb, vgrid, r0, r1);
+  __syncthreads();
+  for (int64_t t0 = r0; t0 < r1; t0 += kT) {
+    const int64_t r = t0 + threadIdx.x;
+    float ip32 = 0.f;
+    float* trow = tile + threadIdx.x * LD;
+    if (r < r1) {
+      float n[RT];
+      load_row<RT>(N, r, R, n);
+      T* frow = F + r * R;
+#pragma unroll
+      for (int h = 0; h < RT / CW; ++h) {
+        float o[CW];
+        row_solve<RT, CW>(n, Ws, h * CW, o);
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          const int col = h * CW + c;
+          const float x = o[c] * s_sc[col];
+          const float v = col < R ? rt_elem(F, x) : 0.f;
+          if (col < R) st_elem(frow + col, x);
+          ip32 = fmaf(s_lm[col] * v, n[col], ip32);
+          o[c] = v;
+        }
+#pragma unroll
+        for (int c4 = 0; c4 < CW / 4; ++c4)
+          *reinterpret_cast<float4*>(trow + h * CW + 4 * c4) =
+              make_float4(o[4 * c4], o[4 * c4 + 1], o[4 * c4 + 2], o[4 * c4 + 3]);
+      }
+    } else {
+#pragma unroll
+      for (int c4 = 0; c4 < NB4; ++c4)
+        *reinterpret_cast<float4*>(trow + 4 * c4) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    ip += (double)ip32;
+    __syncthreads();
+    const int nt = (int)min((int64_t)kT, r1 - t0);
+    for (int i = grp; i < nt; i += NGRP) {
+      const float4 xv = *reinterpret_cast<const float4*>(tile + i * LD + 4 * bi);
+      const float4 yv = *reinterpret_cast<const float4*>(tile + i * LD + 4 * bj);
+      const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) a32[u * 4 + w] = fmaf(xa[u], ya[w], a32[u * 4 + w]);
+    }
+    __syncthreads();
+  }
+  if (with_ip) {
+    const double t = block_sum(ip, red);
+    if (threadIdx.x == 0) ipart[vb] = t;
+  }
+  // Add the groups of each block in group order, four entries at a time
+  // through the tile ([kT][4] doubles = 8 KB <= the tile's kT * LD floats).
+  double* rsm = reinterpret_cast<double*>(tile);
+  for (int q0 = 0; q0 < 16; q0 += 4) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) rsm[threadIdx.x * 4 + q] = (double)a32[q0 + q];
+    __syncthreads();
+    if (grp == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double t = 0.0;
+        for (int gg = 0; gg < NGRP; ++gg) t += rsm[(gg * NBLK + blk) * 4 + q];
+        const int e = q0 + q;
+        const int a = 4 * bi + e / 4, c = 4 * bj + e % 4;
+        if (a < R && c < R) gpart[(size_t)vb * R * R + a * R + c] = t;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int RT>
+__global__ void __launch_bounds__(kT, 2) colnorm_rows(const float* __restrict__ N,
+                                                   const float* __restrict__ W32, int64_t rows, int R,
+                                                   double* __restrict__ colsq) {
+  colnorm_rows_body<RT>(N, W32, rows, R, colsq, blockIdx.x, gridDim.x);
+}
+
+template <typename T, int RT>
+__global__ void __launch_bounds__(kT, 2) scale_store_rows(const float* __restrict__ N,
+                                                       const float* __restrict__ W32,
+                                                       const float* __restrict__ inv,
+                                                       const double* __restrict__ lambda,
+                                                       int64_t rows, int R, T* __restrict__ F,
+                                                       double* __restrict__ gpart, bool with_ip,
+                                                       double* __restrict__ ipart) {
+  scale_store_rows_body<T, RT>(N, W32, inv, lambda, rows, R, F, gpart, with_ip, ipart, blockIdx.x,
+                               gridDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// Batched launches: one launch per step for every job of a rank class.  Each
+// block finds its job and its position inside the job and runs the per-job
+// body with that position, so every job gets exactly what its own launch
+// would compute.
+// ---------------------------------------------------------------------------
+
+// Job of block b: the last j with begin[j] <= b.
+__device__ __forceinline__ int job_of_block(const int32_t* __restrict__ begin, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (begin[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) gamma_inverse_batch(const DenseJob* __restrict__ jobs, int R,
+                                                          bool in_smem) {
+  const DenseJob& J = jobs[blockIdx.x];
+  gamma_inverse_body(J.Gf, J.Gi, R, J.lambda_reg, J.W, J.W32, J.singular, J.rr_work, in_smem);
+}
+
+__global__ void __launch_bounds__(kT) als_solve_rows_batch(const DenseJob* __restrict__ jobs,
+                                                           const int32_t* __restrict__ begin, int n,
+                                                           int R) {
+  const int j = job_of_block(begin, n, blockIdx.x);
+  const DenseJob& J = jobs[j];
+  als_solve_rows_body(J.N, J.W32, J.rows, R, J.Fh, J.partials, blockIdx.x - begin[j], J.nb);
+}
+
+template <int RT>
+__global__ void __launch_bounds__(kT, 2) colnorm_rows_batch(const DenseJob* __restrict__ jobs,
+                                                         const int32_t* __restrict__ begin, int n,
+                                                         int R) {
+  const int j = job_of_block(begin, n, blockIdx.x);
+  const DenseJob& J = jobs[j];
+  colnorm_rows_body<RT>(J.N, J.W32, J.rows, R, J.partials, blockIdx.x - begin[j], J.nb);
+}
+
+template <typename T, int RT>
+__global__ void __launch_bounds__(kT, 2) scale_store_rows_batch(const DenseJob* __restrict__ jobs,
+                                                             const int32_t* __restrict__ begin, int n,
+                                                             int R, bool last) {
+  const int j = job_of_block(begin, n, blockIdx.x);
+  const DenseJob& J = jobs[j];
+  scale_store_rows_body<T, RT>(J.N, J.W32, J.inv_lambda, J.lambda, J.rows, R, static_cast<T*>(J.F),
+                               J.partials, last, J.ipart, blockIdx.x - begin[j], J.nb);
+}
+
+__global__ void __launch_bounds__(kT) finish_lambda_batch(const DenseJob* __restrict__ jobs, int R) {
+  const DenseJob& J = jobs[blockIdx.x / R];
+  finish_lambda_body(J.partials, J.nb, R, J.lambda, J.inv_lambda, blockIdx.x % R);
+}
+
+template <typename T, int BPT>
+__global__ void __launch_bounds__(kT) als_store_rows_batch(const DenseJob* __restrict__ jobs,
+                                                           const int32_t* __restrict__ begin, int n,
+                                                           int R, bool last) {
+  const int j = job_of_block(begin, n, blockIdx.x);
+  const DenseJob& J = jobs[j];
+  als_store_rows_body<T, BPT>(J.Fh, J.inv_lambda, J.lambda, J.rows, R, static_cast<T*>(J.F),
+                              J.partials, last ? J.N : nullptr, J.ipart, blockIdx.x - begin[j], J.nb);
+}
+
+__global__ void __launch_bounds__(kT) reduce_partials_batch(const DenseJob* __restrict__ jobs, int R,
+                                                            int per_job) {
+  const DenseJob& J = jobs[blockIdx.x / per_job];
+  reduce_partials_body(J.partials, J.nb, R * R, R, false, J.gram_out, blockIdx.x % per_job);
+}
+
+__global__ void __launch_bounds__(kT) fit_from_parts_batch(const DenseJob* __restrict__ jobs, int R) {
+  const DenseJob& J = jobs[blockIdx.x];
+  fit_from_parts_body(J.ipart, J.nb, R, J.lambda, J.GA, J.GB, J.GC, J.scal);
+}
+
 }  // namespace
+
+int dense_row_blocks(int64_t rows, int R) { return R <= 32 ? pass_blocks(rows) : (int)row_blocks(rows); }
 
 // ---------------------------------------------------------------------------
 // Host orchestration.
@@ -872,12 +1231,38 @@ dfacto_status gram_of_factor(dfacto_t* h, int m) {
 
 namespace {
 
+// The row passes of one mode for R <= 32 (one thread per row).
+template <typename T, int RT>
+dfacto_status als_post_rows(dfacto_t* h, int mode, float* N) {
+  const int R = h->R;
+  cudaStream_t s = h->stream;
+  const int64_t rows = h->m[mode].dim_o;
+  const int nb = pass_blocks(rows);
+  const bool last = (mode == 2);
+  colnorm_rows<RT><<<nb, kT, 0, s>>>(N, h->W32, rows, R, h->partials);
+  DF_COUNT();
+  finish_lambda<<<R, kT, 0, s>>>(h->partials, nb, R, h->lambda, h->inv_lambda);
+  DF_COUNT();
+  scale_store_rows<T, RT><<<nb, kT, 0, s>>>(N, h->W32, h->inv_lambda, h->lambda, rows, R,
+                                            static_cast<T*>(h->F[mode]), h->partials, last, h->ipart);
+  DF_COUNT();
+  reduce_partials<<<(R * R + 31) / 32, kT, 0, s>>>(h->partials, nb, R * R, R, false, h->gram[mode]);
+  DF_COUNT();
+  DF_CUDA(h, cudaGetLastError());
+  h->gram_valid[mode] = true;
+  if (last) h->ipart_blocks = nb;
+  return DFACTO_OK;
+}
+
 template <typename T>
 dfacto_status als_post_T(dfacto_t* h, int mode, float* N) {
   const ModeCSR& M = h->m[mode];
   const int R = h->R;
   const int R4 = (R + 3) / 4;
   cudaStream_t s = h->stream;
+  if (R <= 8) return als_post_rows<T, 8>(h, mode, N);
+  if (R <= 16) return als_post_rows<T, 16>(h, mode, N);
+  if (R <= 32) return als_post_rows<T, 32>(h, mode, N);
   const int64_t rows = M.dim_o;
   const unsigned nb = row_blocks(rows);
   const size_t smem_a = solve_bytes(R);
@@ -1029,6 +1414,76 @@ dfacto_status gd_step_T(dfacto_t* h) {
 
 dfacto_status gd_step(dfacto_t* h) {
   return h->dtype == DFACTO_BF16 ? gd_step_T<__nv_bfloat16>(h) : gd_step_T<float>(h);
+}
+
+cudaError_t batch_gamma_inverse(const DenseJob* jobs, int n, int R, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const size_t need = sizeof(double) * (2 * (size_t)R * R + R);
+  const bool in_smem = need <= 48 * 1024;
+  gamma_inverse_batch<<<n, 256, in_smem ? need : 0, s>>>(jobs, R, in_smem);
+  DF_COUNT();
+  return cudaGetLastError();
+}
+
+namespace {
+template <int RT>
+void batch_post_rows(const DenseJob* jobs, const int32_t* begin, int n, int total_blocks, int R,
+                     int dtype, bool last, cudaStream_t s) {
+  colnorm_rows_batch<RT><<<total_blocks, kT, 0, s>>>(jobs, begin, n, R);
+  DF_COUNT();
+  finish_lambda_batch<<<n * R, kT, 0, s>>>(jobs, R);
+  DF_COUNT();
+  if (dtype == DFACTO_BF16)
+    scale_store_rows_batch<__nv_bfloat16, RT><<<total_blocks, kT, 0, s>>>(jobs, begin, n, R, last);
+  else
+    scale_store_rows_batch<float, RT><<<total_blocks, kT, 0, s>>>(jobs, begin, n, R, last);
+  DF_COUNT();
+  const int per_job = (R * R + 31) / 32;
+  reduce_partials_batch<<<n * per_job, kT, 0, s>>>(jobs, R, per_job);
+  DF_COUNT();
+}
+}  // namespace
+
+cudaError_t batch_als_post(const DenseJob* jobs, const int32_t* begin, int n, int total_blocks, int R,
+                           int dtype, bool last, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (R <= 32) {
+    if (R <= 8) batch_post_rows<8>(jobs, begin, n, total_blocks, R, dtype, last, s);
+    else if (R <= 16) batch_post_rows<16>(jobs, begin, n, total_blocks, R, dtype, last, s);
+    else batch_post_rows<32>(jobs, begin, n, total_blocks, R, dtype, last, s);
+    return cudaGetLastError();
+  }
+  const int R4 = (R + 3) / 4;
+  const size_t smem_a = solve_bytes(R);
+  allow_smem(als_solve_rows_batch, smem_a);
+  als_solve_rows_batch<<<total_blocks, kT, smem_a, s>>>(jobs, begin, n, R);
+  DF_COUNT();
+  finish_lambda_batch<<<n * R, kT, 0, s>>>(jobs, R);
+  DF_COUNT();
+  const size_t smem_b = tile_bytes(R, 1);
+  auto store = [&](auto kernel) {
+    allow_smem(kernel, smem_b);
+    kernel<<<total_blocks, kT, smem_b, s>>>(jobs, begin, n, R, last);
+    DF_COUNT();
+  };
+  if (dtype == DFACTO_BF16) {
+    if (R4 * R4 <= kT) store(als_store_rows_batch<__nv_bfloat16, 1>);
+    else store(als_store_rows_batch<__nv_bfloat16, 4>);
+  } else {
+    if (R4 * R4 <= kT) store(als_store_rows_batch<float, 1>);
+    else store(als_store_rows_batch<float, 4>);
+  }
+  const int per_job = (R * R + 31) / 32;
+  reduce_partials_batch<<<n * per_job, kT, 0, s>>>(jobs, R, per_job);
+  DF_COUNT();
+  return cudaGetLastError();
+}
+
+cudaError_t batch_fit(const DenseJob* jobs, int n, int R, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  fit_from_parts_batch<<<n, kT, 0, s>>>(jobs, R);
+  DF_COUNT();
+  return cudaGetLastError();
 }
 
 }  // namespace dfacto

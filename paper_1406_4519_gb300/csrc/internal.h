@@ -142,7 +142,42 @@ dfacto_status ensure_segments(dfacto_t* h, int mode);
 WalkCfg choose_walk(int R, int dtype, int64_t nnz, int64_t nfib, int seg_opt, int vec_opt);
 dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out);
 
-// ---- batches (batch.cu) ---------------------------------------------------
+// ---- batches (batch.cu, dense.cu) -----------------------------------------
+// One job of a batch for one mode, as the batched R x R and row kernels see
+// it: the pointers the per-job kernels would take from the job's handle.
+struct DenseJob {
+  const double* Gf;        // Gram of factor f
+  const double* Gi;        // Gram of factor in
+  double lambda_reg;
+  double* W;               // Gamma^{-1} (FP64), [R x R]
+  float* W32;              // Gamma^{-1} (FP32)
+  int32_t* singular;       // the job's singular flag
+  double* rr_work;         // R x R solve workspace
+  const float* N;          // MTTKRP output rows of the job, [rows x R]
+  int64_t rows;            // dims[mode]
+  int nb;                  // row blocks of the row passes
+  float* Fh;               // N Gamma^{-1} (R > 32 only)
+  double* partials;        // per-block partials
+  double* lambda;          // [R]
+  float* inv_lambda;       // [R]
+  void* F;                 // the factor of this mode (storage type)
+  double* gram_out;        // Gram of the new factor
+  double* ipart;           // partials of <X, Xhat> (mode 3)
+  const double* GA;        // Grams of the three factors (fit)
+  const double* GB;
+  const double* GC;
+  double* scal;            // the job's scalars
+};
+int dense_row_blocks(int64_t rows, int R);  // blocks of the row passes of one mode
+// Batched steps of one rank class (all jobs share R and the factor type):
+// Gamma^{-1} of every job; N Gamma^{-1}, normalisation, store and Gram (and on
+// the last mode the fit's inner product); the fit.  begin[j] is the first row
+// block of job j (prefix sums of nb, begin[n] = total).
+cudaError_t batch_gamma_inverse(const DenseJob* jobs, int n, int R, cudaStream_t s);
+cudaError_t batch_als_post(const DenseJob* jobs, const int32_t* begin, int n, int total_blocks, int R,
+                           int dtype, bool last, cudaStream_t s);
+cudaError_t batch_fit(const DenseJob* jobs, int n, int R, cudaStream_t s);
+
 // Called by dfacto_destroy for a handle still in a batch: the batch drops it.
 void batch_forget(dfacto_batch* b, dfacto_t* h);
 

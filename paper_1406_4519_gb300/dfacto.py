@@ -53,8 +53,8 @@ class dfacto_csr_view(ctypes.Structure):
 
 
 class dfacto_batch_options(ctypes.Structure):
-    _fields_ = [("side_streams", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+    _fields_ = [("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class dfacto_batch_class(ctypes.Structure):
@@ -346,12 +346,9 @@ class Tensor:
 
 # ---- batches -----------------------------------------------------------------
 
-def dfacto_batch_options_init(side_streams: int = 0, use_graph: bool = True,
-                              autotune: bool = True) -> dfacto_batch_options:
+def dfacto_batch_options_init(use_graph: bool = True, autotune: bool = True) -> dfacto_batch_options:
     opt = dfacto_batch_options()
     load().dfacto_batch_options_init(ctypes.byref(opt))
-    if side_streams:
-        opt.side_streams = int(side_streams)
     opt.use_graph = int(bool(use_graph))
     opt.autotune = int(bool(autotune))
     return opt
@@ -402,10 +399,10 @@ class Batch:
     """Owning wrapper of a batch of Tensor jobs.  Holds references to the jobs
     so that they outlive the batch (the batch must be destroyed first)."""
 
-    def __init__(self, tensors: Sequence["Tensor"], side_streams: int = 0, use_graph: bool = True,
-                 autotune: bool = True, stream=None):
+    def __init__(self, tensors: Sequence["Tensor"], use_graph: bool = True, autotune: bool = True,
+                 stream=None):
         self.tensors = list(tensors)
-        self.opt = dfacto_batch_options_init(side_streams, use_graph, autotune)
+        self.opt = dfacto_batch_options_init(use_graph, autotune)
         self.b = dfacto_batch_create([t.h for t in self.tensors], self.opt, stream)
 
     def close(self) -> None:

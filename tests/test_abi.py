@@ -121,4 +121,4 @@ def test_batch_host_side_argument_checks(lib):
     assert lib.dfacto_batch_get_class(None, 0, ctypes.byref(c)) == dfacto.EINVAL
     lib.dfacto_batch_destroy(None)
     opt = dfacto.dfacto_batch_options_init()
-    assert (opt.side_streams, opt.use_graph, opt.autotune) == (16, 1, 1)
+    assert (opt.use_graph, opt.autotune) == (1, 1)
