@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "device.cuh"
@@ -25,10 +26,32 @@ dfacto_status cuda_fail(dfacto_t* h, cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? DFACTO_ENOMEM : DFACTO_ECUDA;
 }
 
+// Device memory of a handle comes from the device's stream-ordered pool
+// (cudaMallocAsync on the handle's stream): allocation and release do not
+// synchronize the device, so building and destroying many small handles (a
+// serving loop) does not stall the work of others.  Freed memory stays cached
+// in the pool for the next handle (release threshold raised once per device).
+void keep_pool_memory() {
+  static std::once_flag once[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  std::call_once(once[dev], [dev]() {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+  });
+}
+
 dfacto_status dalloc(dfacto_t* h, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = cudaMallocAsync(p, bytes, h->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -41,7 +64,7 @@ dfacto_status dalloc(dfacto_t* h, void** p, size_t bytes) {
 
 void dfree(dfacto_t* h, void* p, size_t bytes) {
   if (!p) return;
-  cudaFree(p);
+  cudaFreeAsync(p, h->stream);
   if (bytes == 0) bytes = 16;
   h->bytes -= (int64_t)bytes;
 }
@@ -202,34 +225,17 @@ void dfacto_destroy(dfacto_t* h) {
   }
   for (int m = 0; m < 3; ++m) {
     ModeCSR& M = h->m[m];
-    cudaFree(M.fiber_ptr);
-    cudaFree(M.fiber_idx);
-    cudaFree(M.fiber_row);
-    cudaFree(M.nz_ptr);
-    cudaFree(M.nz_idx);
-    cudaFree(M.nz_val);
-    cudaFree(M.end_bits);
-    cudaFree(M.seg_fib);
-    cudaFree(h->F[m]);
-    cudaFree(h->grad[m]);
-    cudaFree(h->gram[m]);
+    for (void* q : {(void*)M.fiber_ptr, (void*)M.fiber_idx, (void*)M.fiber_row, (void*)M.nz_ptr,
+                    (void*)M.nz_idx, (void*)M.nz_val, (void*)M.end_bits, (void*)M.seg_fib,
+                    h->F[m], (void*)h->grad[m], (void*)h->gram[m]})
+      if (q) cudaFreeAsync(q, h->stream);
   }
-  cudaFree(h->N);
-  cudaFree(h->Fh);
-  cudaFree(h->lambda);
-  cudaFree(h->inv_lambda);
-  cudaFree(h->ipart);
-  cudaFree(h->gd_mats);
-  cudaFree(h->W);
-  cudaFree(h->rr_work);
-  cudaFree(h->W32);
-  cudaFree(h->scal);
-  cudaFree(h->flags);
-  cudaFree(h->partials);
-  cudaFree(h->carry);
-  cudaFree(h->carry_row);
-  cudaFreeHost(h->host_scal);
-  cudaFreeHost(h->host_flags);
+  for (void* q : {(void*)h->N, (void*)h->Fh, (void*)h->lambda, (void*)h->inv_lambda, (void*)h->ipart,
+                  (void*)h->gd_mats, (void*)h->W, (void*)h->rr_work, (void*)h->W32, (void*)h->scal,
+                  (void*)h->flags, (void*)h->partials, (void*)h->carry, (void*)h->carry_row})
+    if (q) cudaFreeAsync(q, h->stream);
+  delete[] h->host_scal;
+  delete[] h->host_flags;
   cudaGetLastError();
   delete h;
 }
@@ -260,6 +266,7 @@ dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, co
 
   dfacto_t* h = new (std::nothrow) dfacto_handle();
   if (!h) return DFACTO_ENOMEM;
+  keep_pool_memory();
   h->stream = static_cast<cudaStream_t>(stream);
   cudaGetDevice(&h->device);
   std::memcpy(h->dims, dims, sizeof(int32_t) * 3);
@@ -286,16 +293,15 @@ dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, co
   if ((st = dalloc(h, (void**)&h->rr_work, sizeof(double) * (2 * RR + R))) != DFACTO_OK) return bail(st);
   if ((st = dalloc(h, (void**)&h->W32, sizeof(float) * RR)) != DFACTO_OK) return bail(st);
   if ((st = dalloc(h, (void**)&h->N, sizeof(float) * maxdim * R)) != DFACTO_OK) return bail(st);
-  if ((st = dalloc(h, (void**)&h->Fh, sizeof(float) * maxdim * R)) != DFACTO_OK) return bail(st);
+  if (R > 32 && (st = dalloc(h, (void**)&h->Fh, sizeof(float) * maxdim * R)) != DFACTO_OK)
+    return bail(st);  // N Gamma^{-1} is stored only by the row passes for R > 32
   for (int m = 0; m < 3; ++m) {
     if ((st = dalloc(h, &h->F[m], elem_size(h->dtype) * (size_t)dims[m] * R)) != DFACTO_OK) return bail(st);
     if ((st = dalloc(h, (void**)&h->gram[m], sizeof(double) * RR)) != DFACTO_OK) return bail(st);
   }
-  if (cudaMallocHost((void**)&h->host_scal, sizeof(double) * kNumScalars) != cudaSuccess ||
-      cudaMallocHost((void**)&h->host_flags, sizeof(int32_t) * kNumFlags) != cudaSuccess) {
-    cudaGetLastError();
-    return bail(DFACTO_ENOMEM);
-  }
+  h->host_scal = new (std::nothrow) double[kNumScalars]();
+  h->host_flags = new (std::nothrow) int32_t[kNumFlags]();
+  if (!h->host_scal || !h->host_flags) return bail(DFACTO_ENOMEM);
   cudaStream_t s = h->stream;
   if (cudaMemsetAsync(h->scal, 0, sizeof(double) * kNumScalars, s) != cudaSuccess) return bail(DFACTO_ECUDA);
   for (int m = 0; m < 3; ++m)

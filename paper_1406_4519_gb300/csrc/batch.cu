@@ -145,8 +145,8 @@ struct dfacto_batch {
   double* d_fits = nullptr;      // [n]
   int32_t* d_status = nullptr;   // [n]
   int32_t* d_bad = nullptr;      // fix-up consistency flag
-  double* h_fits = nullptr;      // pinned [n]
-  int32_t* h_status = nullptr;   // pinned [n]
+  double* h_fits = nullptr;      // host [n]
+  int32_t* h_status = nullptr;   // host [n]
   std::vector<void*> owned;      // device allocations of the batch
   std::string err;
 };
@@ -171,10 +171,12 @@ dfacto_status bcuda(dfacto_batch* b, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return bcuda((b), e_, #call); \
   } while (0)
 
+// Batch memory comes from the device's stream-ordered pool, on the batch's
+// main stream (freed there when the batch is destroyed).
 template <typename P>
 dfacto_status balloc(dfacto_batch* b, P** p, size_t bytes) {
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, std::max<size_t>(bytes, 16));
+  cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(bytes, 16), b->main);
   if (e != cudaSuccess) {
     *p = nullptr;
     return bcuda(b, e, "cudaMalloc (batch)");
@@ -528,8 +530,9 @@ dfacto_status enter(dfacto_batch* b) {
 }
 
 void release(dfacto_batch* b) {
-  for (void* p : b->owned) cudaFree(p);
+  for (void* p : b->owned) cudaFreeAsync(p, b->main);
   b->owned.clear();
+  if (b->main) cudaStreamSynchronize(b->main);
   drop_graph(b);
   if (b->side) cudaStreamDestroy(b->side);
   if (b->side_ev) cudaEventDestroy(b->side_ev);
@@ -537,8 +540,8 @@ void release(dfacto_batch* b) {
   b->side_ev = nullptr;
   if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   if (b->main) cudaStreamDestroy(b->main);
-  if (b->h_fits) cudaFreeHost(b->h_fits);
-  if (b->h_status) cudaFreeHost(b->h_status);
+  delete[] b->h_fits;
+  delete[] b->h_status;
   b->fork_ev = nullptr;
   b->main = nullptr;
   b->h_fits = nullptr;
@@ -546,8 +549,10 @@ void release(dfacto_batch* b) {
   cudaGetLastError();
 }
 
-// Give every job its factors back in allocations of its own.
+// Give every job its factors back in allocations of its own (allocated and
+// copied on the job's stream, after the batch's work).
 void unpool(dfacto_batch* b) {
+  if (b->main) cudaStreamSynchronize(b->main);
   for (BatchClass& C : b->cls) {
     for (size_t t = 0; t < C.jobs.size(); ++t) {
       dfacto_t* h = b->jobs[C.jobs[t]];
@@ -556,7 +561,7 @@ void unpool(dfacto_batch* b) {
         const size_t bytes = elem_bytes(C.dtype) * (size_t)h->dims[m] * C.R;
         void* p = nullptr;
         if (dalloc(h, &p, bytes) == DFACTO_OK) {
-          cudaMemcpyAsync(p, h->F[m], bytes, cudaMemcpyDeviceToDevice, b->main);
+          cudaMemcpyAsync(p, h->F[m], bytes, cudaMemcpyDeviceToDevice, h->stream);
           h->F[m] = p;
         } else {
           h->F[m] = nullptr;  // out of memory: the job has lost its factors
@@ -565,7 +570,8 @@ void unpool(dfacto_batch* b) {
       h->batch = nullptr;
     }
   }
-  if (b->main) cudaStreamSynchronize(b->main);
+  for (dfacto_t* h : b->jobs)
+    if (h) cudaStreamSynchronize(h->stream);
 }
 
 }  // namespace
@@ -689,9 +695,9 @@ dfacto_status dfacto_batch_create(dfacto_t* const* jobs, int32_t n, const dfacto
   if ((st = balloc(b, &b->d_fits, sizeof(double) * n)) != DFACTO_OK) return bail(st);
   if ((st = balloc(b, &b->d_status, sizeof(int32_t) * n)) != DFACTO_OK) return bail(st);
   if ((st = balloc(b, &b->d_bad, sizeof(int32_t))) != DFACTO_OK) return bail(st);
-  if (cudaMallocHost(&b->h_fits, sizeof(double) * n) != cudaSuccess ||
-      cudaMallocHost(&b->h_status, sizeof(int32_t) * n) != cudaSuccess)
-    return bail(DFACTO_ENOMEM);
+  b->h_fits = new (std::nothrow) double[n]();
+  b->h_status = new (std::nothrow) int32_t[n]();
+  if (!b->h_fits || !b->h_status) return bail(DFACTO_ENOMEM);
   {
     std::vector<double*> sc(n);
     std::vector<int32_t*> fl(n);

@@ -99,8 +99,8 @@ struct dfacto_handle {
   float* carry = nullptr;                     // MTTKRP CTA carries [ncta x 2 x R]
   int32_t* carry_row = nullptr;               // [ncta x 4] head row, tail row, slot info
   int64_t carry_cap = 0;                      // CTAs
-  double* host_scal = nullptr;                // pinned mirror of scal
-  int32_t* host_flags = nullptr;              // pinned mirror of flags
+  double* host_scal = nullptr;                // host mirror of scal
+  int32_t* host_flags = nullptr;              // host mirror of flags
   int64_t bytes = 0;
   std::string err;
   // Set while the handle is in a batch: F[m] then point into the batch's

@@ -1,0 +1,284 @@
+"""Serving many decompositions: continuous batching of CP-ALS jobs.
+
+Jobs (sparse 3-way tensors with a rank) arrive over time.  The server keeps
+every admitted job resident on the GPU (its flattened CSR copies and factors),
+advances all admitted jobs together one ALS sweep (Algorithm 4) at a time
+through a batch (dfacto_batch_*), and retires a job when its fit stops moving
+(|fit - previous fit| < tol) or after max_iters sweeps; the job's result is its
+factors and weights, copied to the host at retirement.
+
+Admission is first come, first served under a device-memory budget: a job is
+admitted when the estimated footprint of everything admitted stays within the
+budget.  Membership changes (admissions, retirements) take effect when the
+batch is rebuilt, at most once per `rebuild_interval` seconds, so that a burst
+of arrivals does not rebuild the batch after every sweep.
+
+The scheduling decisions live in `Scheduler` (pure Python, no GPU), the device
+work in `GpuEngine`; `serve()` runs the loop in real time against a list of
+arrival times.  `serve_sequential()` is the comparison: one job at a time, in
+arrival order, each with its own single-tensor ALS loop.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional, Sequence
+
+
+@dataclass
+class JobSpec:
+    """One request: a tensor (COO on the device), its rank and start factors."""
+    job_id: int
+    arrival: float                 # seconds from the start of the run
+    dims: Sequence[int]
+    nnz: int
+    rank: int
+    make: Callable                 # () -> (idx, val, factors): device tensors
+
+
+@dataclass
+class JobState:
+    spec: JobSpec
+    admitted_at: Optional[float] = None
+    finished_at: Optional[float] = None
+    iters: int = 0
+    fits: List[float] = field(default_factory=list)
+    footprint: int = 0
+    result: Optional[dict] = None
+
+    @property
+    def latency(self) -> Optional[float]:
+        if self.finished_at is None:
+            return None
+        return self.finished_at - self.spec.arrival
+
+
+def footprint_bytes(dims: Sequence[int], nnz: int, rank: int, factor_bytes: int) -> int:
+    """Upper estimate of the device bytes a job holds while it is served: the
+    CSR copies of its three modes twice (the job's own and the batch's
+    concatenated copy; per mode 8 bytes per nonzero for (index, value), at most
+    one fiber per nonzero at 16 bytes, 8 bytes per row pointer, end bits), the
+    factors (own and pooled), the MTTKRP outputs, and the row-pass buffers."""
+    sd = sum(int(d) for d in dims)
+    csr = 3 * (8 * nnz + 16 * nnz + nnz // 8 + 4 * nnz // 32) + 8 * (sd + 3)
+    factors = factor_bytes * rank * sd
+    rows = 4 * rank * sd + 2 * 4 * rank * max(dims)
+    return 2 * csr + 2 * factors + rows + (1 << 20)
+
+
+class Scheduler:
+    """Admission, retirement and rebuild decisions; no device work."""
+
+    def __init__(self, budget_bytes: float, max_iters: int = 50, tol: float = 1e-4,
+                 rebuild_interval: float = 0.005, factor_bytes: int = 2):
+        self.budget = float(budget_bytes)
+        self.max_iters = int(max_iters)
+        self.tol = float(tol)
+        self.rebuild_interval = float(rebuild_interval)
+        self.factor_bytes = int(factor_bytes)
+        self.pending: List[JobState] = []    # arrived, not admitted (FIFO)
+        self.active: Dict[int, JobState] = {}  # admitted, not finished
+        self.done: List[JobState] = []
+        self.used = 0
+        self.last_rebuild = -1e30
+
+    def arrive(self, job: JobState) -> None:
+        job.footprint = footprint_bytes(job.spec.dims, job.spec.nnz, job.spec.rank, self.factor_bytes)
+        self.pending.append(job)
+
+    def admissible(self) -> List[JobState]:
+        """Pending jobs to admit now, first come first served: stop at the first
+        job that does not fit (no overtaking).  A job larger than the whole
+        budget is admitted alone once nothing else is resident."""
+        out = []
+        used = self.used
+        for job in self.pending:
+            if used + job.footprint <= self.budget or (used == 0 and not out):
+                out.append(job)
+                used += job.footprint
+            else:
+                break
+        return out
+
+    def admit(self, jobs: Sequence[JobState], now: float) -> None:
+        for job in jobs:
+            self.pending.remove(job)
+            job.admitted_at = now
+            self.active[job.spec.job_id] = job
+            self.used += job.footprint
+
+    def record_sweep(self, fits: Dict[int, float]) -> List[JobState]:
+        """Record one sweep's fits; return the jobs that are now finished
+        (|fit change| < tol, or max_iters sweeps)."""
+        finished = []
+        for jid, fit in fits.items():
+            job = self.active[jid]
+            job.iters += 1
+            job.fits.append(float(fit))
+            converged = len(job.fits) >= 2 and abs(job.fits[-1] - job.fits[-2]) < self.tol
+            if converged or job.iters >= self.max_iters:
+                finished.append(job)
+        return finished
+
+    def retire(self, job: JobState, now: float) -> None:
+        job.finished_at = now
+        del self.active[job.spec.job_id]
+        self.used -= job.footprint
+        self.done.append(job)
+
+    def should_rebuild(self, now: float, membership_changed: bool, have_batch: bool) -> bool:
+        if not membership_changed:
+            return False
+        if not have_batch:
+            return True
+        return now - self.last_rebuild >= self.rebuild_interval
+
+
+class GpuEngine:
+    """Device side of the server: builds jobs, keeps one batch of the admitted
+    jobs, runs sweeps, reads results."""
+
+    def __init__(self, factor_dtype: int, use_graph: bool = False):
+        from . import dfacto
+        self.dfacto = dfacto
+        self.factor_dtype = factor_dtype
+        # A batch lives from one membership change to the next (a few sweeps),
+        # too short for a captured graph to pay for its capture by default.
+        self.use_graph = use_graph
+        self.tensors: Dict[int, "dfacto.Tensor"] = {}
+        self.batch = None
+        self.members: List[int] = []
+
+    def build(self, job: JobState) -> None:
+        idx, val, F = job.spec.make()
+        t = self.dfacto.Tensor(idx, val, job.spec.dims, rank=job.spec.rank,
+                               factor_dtype=self.factor_dtype)
+        t.set_factors(F)
+        self.tensors[job.spec.job_id] = t
+
+    def rebuild(self, members: Sequence[int]) -> None:
+        if self.batch is not None:
+            self.batch.close()
+            self.batch = None
+        self.members = list(members)
+        if self.members:
+            self.batch = self.dfacto.Batch([self.tensors[j] for j in self.members], autotune=False,
+                                           use_graph=self.use_graph)
+
+    def sweep(self) -> Dict[int, float]:
+        st, fits = self.batch.als_iter(want_fits=True)
+        return dict(zip(self.members, fits))
+
+    def result(self, jid: int) -> dict:
+        import torch
+        t = self.tensors[jid]
+        return {"factors": [f.cpu() for f in t.factors(dtype=torch.float32)], "lambda": t.lam()}
+
+    def release(self, jid: int) -> None:
+        t = self.tensors.pop(jid)
+        if self.batch is not None and jid in self.members:
+            return  # still in the batch: dropped at the next rebuild
+        del t
+
+    def close(self) -> None:
+        if self.batch is not None:
+            self.batch.close()
+            self.batch = None
+
+
+def serve(jobs: Sequence[JobSpec], budget_bytes: float = 120e9, max_iters: int = 50,
+          tol: float = 1e-4, rebuild_interval: float = 0.005, factor_dtype: Optional[int] = None,
+          engine=None, clock: Callable[[], float] = time.perf_counter,
+          sleep: Callable[[float], None] = time.sleep) -> List[JobState]:
+    """Serve `jobs` (sorted by arrival) in real time; returns the finished jobs
+    with their latencies (arrival -> factors on the host)."""
+    if engine is None:
+        from . import dfacto
+        engine = GpuEngine(dfacto.BF16 if factor_dtype is None else factor_dtype)
+    fbytes = 4 if factor_dtype == 0 else 2
+    sch = Scheduler(budget_bytes, max_iters, tol, rebuild_interval, fbytes)
+    order = sorted(jobs, key=lambda j: j.arrival)
+    nxt = 0
+    t0 = clock()
+    retired_in_batch = set()   # finished jobs whose handles still sit in the batch
+    changed = False
+    while nxt < len(order) or sch.pending or sch.active:
+        now = clock() - t0
+        while nxt < len(order) and order[nxt].arrival <= now:
+            sch.arrive(JobState(order[nxt]))
+            nxt += 1
+        adm = sch.admissible()
+        if adm:
+            for job in adm:
+                engine.build(job)
+            sch.admit(adm, clock() - t0)
+            changed = True
+        now = clock() - t0
+        if sch.should_rebuild(now, changed or bool(retired_in_batch), engine.batch is not None):
+            engine.rebuild(sorted(sch.active))
+            for jid in retired_in_batch:
+                engine.release(jid)
+            retired_in_batch.clear()
+            sch.last_rebuild = now
+            changed = False
+        if engine.batch is None or not sch.active:
+            if nxt < len(order):
+                sleep(max(0.0, min(order[nxt].arrival - (clock() - t0), 0.01)))
+            continue
+        fits = engine.sweep()
+        fits = {j: f for j, f in fits.items() if j in sch.active}
+        for job in sch.record_sweep(fits):
+            job.result = engine.result(job.spec.job_id)
+            sch.retire(job, clock() - t0)
+            retired_in_batch.add(job.spec.job_id)
+    engine.close()
+    return sch.done
+
+
+def serve_sequential(jobs: Sequence[JobSpec], max_iters: int = 50, tol: float = 1e-4,
+                     factor_dtype: int = 0, clock: Callable[[], float] = time.perf_counter,
+                     sleep: Callable[[float], None] = time.sleep) -> List[JobState]:
+    """The comparison server: one job at a time in arrival order, each run to
+    convergence with the single-tensor ALS entry point."""
+    import torch
+
+    from . import dfacto
+    order = sorted(jobs, key=lambda j: j.arrival)
+    done = []
+    t0 = clock()
+    for spec in order:
+        now = clock() - t0
+        if spec.arrival > now:
+            sleep(spec.arrival - now)
+        job = JobState(spec, admitted_at=clock() - t0)
+        idx, val, F = spec.make()
+        t = dfacto.Tensor(idx, val, spec.dims, rank=spec.rank, factor_dtype=factor_dtype)
+        t.set_factors(F)
+        while True:
+            st, fit = t.als_iter(want_fit=True)
+            job.iters += 1
+            job.fits.append(fit)
+            if (len(job.fits) >= 2 and abs(job.fits[-1] - job.fits[-2]) < tol) or job.iters >= max_iters:
+                break
+        job.result = {"factors": [f.cpu() for f in t.factors(dtype=torch.float32)], "lambda": t.lam()}
+        job.finished_at = clock() - t0
+        del t
+        done.append(job)
+    return done
+
+
+def latency_stats(done: Sequence[JobState]) -> dict:
+    """p50 / p99 latency and throughput of finished jobs."""
+    lat = sorted(j.latency for j in done if j.latency is not None)
+    if not lat:
+        return {"jobs": 0}
+
+    def pct(p):
+        k = min(len(lat) - 1, max(0, int(round(p / 100.0 * (len(lat) - 1)))))
+        return lat[k]
+
+    first = min(j.spec.arrival for j in done)
+    last = max(j.finished_at for j in done)
+    return {"jobs": len(lat), "p50_s": pct(50), "p99_s": pct(99), "mean_s": sum(lat) / len(lat),
+            "jobs_per_s": len(lat) / max(last - first, 1e-9),
+            "mean_iters": sum(j.iters for j in done) / len(done)}

@@ -1,0 +1,181 @@
+"""Serving loop: the scheduler's decisions on the CPU against a scripted engine
+and a simulated clock, and (GPU) a job served in a mix of jobs gives what the
+same job gives alone."""
+import numpy as np
+import pytest
+
+from paper_1406_4519_gb300 import serve
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(dt, 1e-4)
+
+
+class FakeEngine:
+    """Sweeps cost `sweep_s` simulated seconds; job j's fit after k sweeps is
+    1 - rate_j^k, so it converges (|change| < tol) at a known sweep."""
+
+    def __init__(self, clock, rates, sweep_s=1e-3):
+        self.clock = clock
+        self.rates = rates
+        self.sweep_s = sweep_s
+        self.batch = None
+        self.members = []
+        self.k = {}
+        self.built = []
+        self.rebuilds = 0
+        self.max_members = 0
+
+    def build(self, job):
+        self.built.append(job.spec.job_id)
+        self.k[job.spec.job_id] = 0
+
+    def rebuild(self, members):
+        self.rebuilds += 1
+        self.members = list(members)
+        self.batch = object() if self.members else None
+        self.max_members = max(self.max_members, len(self.members))
+
+    def sweep(self):
+        self.clock.t += self.sweep_s
+        out = {}
+        for j in self.members:
+            self.k[j] += 1
+            out[j] = 1.0 - self.rates[j] ** self.k[j]
+        return out
+
+    def result(self, jid):
+        return {"sweeps": self.k[jid]}
+
+    def release(self, jid):
+        pass
+
+    def close(self):
+        self.batch = None
+
+
+def specs(n, arrivals, nnz=1000, dims=(100, 100, 100), rank=8):
+    return [serve.JobSpec(i, arrivals[i], list(dims), nnz, rank, make=None) for i in range(n)]
+
+
+def converge_sweep(rate, tol):
+    """First k >= 2 with |(1 - rate^k) - (1 - rate^(k-1))| < tol."""
+    k = 2
+    while abs(rate ** k - rate ** (k - 1)) >= tol:
+        k += 1
+    return k
+
+
+def run(jobs, rates, **kw):
+    clock = FakeClock()
+    eng = FakeEngine(clock, rates, kw.pop("sweep_s", 1e-3))
+    done = serve.serve(jobs, engine=eng, clock=clock, sleep=clock.sleep, **kw)
+    return done, eng
+
+
+def test_every_job_finishes_at_its_convergence_sweep_or_the_cap():
+    rates = {0: 0.5, 1: 0.9, 2: 0.99, 3: 0.3}
+    jobs = specs(4, [0.0, 0.001, 0.002, 0.05])
+    done, eng = run(jobs, rates, max_iters=50, tol=1e-4)
+    assert sorted(j.spec.job_id for j in done) == [0, 1, 2, 3]
+    for j in done:
+        want = min(converge_sweep(rates[j.spec.job_id], 1e-4), 50)
+        assert j.iters == want, (j.spec.job_id, j.iters, want)
+        assert j.result["sweeps"] >= j.iters
+        assert j.latency > 0
+
+
+def test_budget_bounds_resident_jobs_and_admission_is_fifo():
+    fp = serve.footprint_bytes([100, 100, 100], 1000, 8, 2)
+    rates = {i: 0.5 for i in range(10)}
+    jobs = specs(10, [0.0] * 10)
+    done, eng = run(jobs, rates, budget_bytes=2.5 * fp, max_iters=50, tol=1e-4)
+    assert eng.max_members <= 2
+    assert eng.built == list(range(10))  # admitted in arrival order, none overtakes
+    assert len(done) == 10
+
+
+def test_job_larger_than_the_budget_runs_alone():
+    rates = {0: 0.5, 1: 0.5}
+    jobs = [serve.JobSpec(0, 0.0, [100, 100, 100], 10 ** 7, 8, make=None),
+            serve.JobSpec(1, 0.0, [100, 100, 100], 1000, 8, make=None)]
+    done, eng = run(jobs, rates, budget_bytes=1e6, max_iters=50, tol=1e-4)
+    assert len(done) == 2 and eng.max_members == 1
+
+
+def test_rebuilds_are_throttled():
+    """Arrivals every 1 ms with a 20 ms rebuild interval: far fewer rebuilds than
+    arrivals, and every job still finishes."""
+    n = 200
+    rates = {i: 0.8 for i in range(n)}
+    jobs = specs(n, [0.001 * i for i in range(n)])
+    done, eng = run(jobs, rates, max_iters=50, tol=1e-4, rebuild_interval=0.02)
+    assert len(done) == n
+    sim_time = max(j.finished_at for j in done)
+    assert eng.rebuilds <= sim_time / 0.02 + 3
+
+
+def test_cap_applies_when_fit_keeps_moving():
+    rates = {0: 0.9999}
+    done, eng = run(specs(1, [0.0]), rates, max_iters=7, tol=1e-12)
+    assert done[0].iters == 7
+
+
+def test_latency_stats():
+    jobs = []
+    for i, lat in enumerate([1.0, 2.0, 3.0, 4.0, 100.0]):
+        st = serve.JobState(serve.JobSpec(i, 0.0, [1, 1, 1], 1, 1, make=None))
+        st.finished_at = lat
+        st.iters = 1
+        jobs.append(st)
+    s = serve.latency_stats(jobs)
+    assert s["jobs"] == 5 and s["p50_s"] == 3.0 and s["p99_s"] == 100.0
+    assert s["jobs_per_s"] == pytest.approx(5 / 100.0)
+
+
+@pytest.mark.gpu
+def test_job_in_the_mix_equals_job_alone():
+    """Five jobs of mixed rank arrive together and in a burst; each is served
+    exactly three sweeps (tol = 0) in FP32.  Its factors equal the same job run
+    alone for three sweeps within 1e-4 normwise (the MTTKRP summation splits
+    differ between the batch and the single tensor, ~1e-6 per sweep)."""
+    import torch
+
+    from paper_1406_4519_gb300 import dfacto, synth
+
+    shapes = [([300, 200, 100], 20000, 8), ([500, 400, 300], 40000, 16), ([80, 60, 40], 3000, 10),
+              ([700, 300, 200], 30000, 32), ([200, 200, 200], 10000, 16)]
+    arrivals = [0.0, 0.0, 0.0, 0.03, 0.031]
+
+    def maker(i):
+        dims, nnz, R = shapes[i]
+
+        def make():
+            idx, val = synth.uniform_tensor(dims, nnz, seed=200 + i, device="cuda")
+            F = synth.normal_factors(dims, R, seed=300 + i, device="cuda")
+            return idx, val, F
+        return make
+
+    jobs = [serve.JobSpec(i, arrivals[i], shapes[i][0], shapes[i][1], shapes[i][2], make=maker(i))
+            for i in range(len(shapes))]
+    done = serve.serve(jobs, max_iters=3, tol=0.0, factor_dtype=dfacto.F32)
+    assert len(done) == len(shapes)
+    for job in done:
+        i = job.spec.job_id
+        assert job.iters == 3
+        idx, val, F = maker(i)()
+        t = dfacto.Tensor(idx, val, shapes[i][0], rank=shapes[i][2])
+        t.set_factors(F)
+        for _ in range(3):
+            t.als_iter()
+        alone = [f.double().cpu().numpy() for f in t.factors()]
+        for m in range(3):
+            got = job.result["factors"][m].double().numpy()
+            assert np.linalg.norm(got - alone[m]) <= 1e-4 * np.linalg.norm(alone[m]), (i, m)
