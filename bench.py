@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark of the DFacTo hot path on one GB300 (or N replicas under torchrun).
 
-Workload (default, "c2"): a 1,000,000 x 500,000 x 200,000 sparse tensor with
+Workload (default, "zipf50M"): a 1,000,000 x 500,000 x 200,000 sparse tensor with
 50,000,000 unique nonzeros whose coordinates are Zipf(1.2) in every mode,
 values = a planted rank-32 CP model (N(0,1) factors) plus 1% Gaussian noise,
 rank R = 32, FP32 factors, N(0,1) starting factors.  Synthetic, seeded; the
@@ -35,13 +35,17 @@ if ROOT not in sys.path:
 
 METRIC = "ALS iter/s"
 WORKLOADS = {
-    "c2": dict(desc="Zipf(1.2) 1000000x500000x200000, 50M unique nnz, planted rank-32 CP + 1% "
-                    "noise, R=32, N(0,1) init",
-               dims=[1_000_000, 500_000, 200_000], nnz=50_000_000, zipf=[1.2, 1.2, 1.2],
-               values="cp", R=32, seed=14064521),
-    "c1": dict(desc="uniform 200x150x100, 10k unique nnz, U(0,1) values, R=10, N(0,1) init",
-               dims=[200, 150, 100], nnz=10_000, zipf=None, values="uniform", R=10,
-               seed=14064520),
+    "zipf50M": dict(desc="Zipf(1.2) 1000000x500000x200000, 50M unique nnz, planted rank-32 CP + "
+                         "1% noise, R=32, N(0,1) init",
+                    dims=[1_000_000, 500_000, 200_000], nnz=50_000_000, zipf=[1.2, 1.2, 1.2],
+                    values="cp", R=32, seed=14064521),
+    "uniform10k": dict(desc="uniform 200x150x100, 10k unique nnz, U(0,1) values, R=10, N(0,1) init",
+                       dims=[200, 150, 100], nnz=10_000, zipf=None, values="uniform", R=10,
+                       seed=14064520),
+    "zipf1200M": dict(desc="Zipf(1.1/1.3/1.2) 6500000x2500000x1500000, 1.2B unique nnz, "
+                           "lognormal(0,1) values, R=10, N(0,1) init",
+                      dims=[6_500_000, 2_500_000, 1_500_000], nnz=1_200_000_000,
+                      zipf=[1.1, 1.3, 1.2], values="lognormal", R=10, seed=14064522),
 }
 # Batch of independent jobs: job shapes from synth.batch_job_specs (dims
 # log-uniform in [1e3, 2e5], nnz lognormal(ln 5e5, 1) clipped to [1e4, 5e6],
@@ -71,7 +75,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2",
+    ap.add_argument("--workload", default="zipf50M",
                     choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(SERVE_WORKLOADS))
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
