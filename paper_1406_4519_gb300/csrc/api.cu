@@ -236,6 +236,12 @@ void dfacto_destroy(dfacto_t* h) {
     if (q) cudaFreeAsync(q, h->stream);
   delete[] h->host_scal;
   delete[] h->host_flags;
+  if (h->aux) {
+    cudaStreamSynchronize(h->aux);
+    cudaStreamDestroy(h->aux);
+  }
+  if (h->aux_fork) cudaEventDestroy(h->aux_fork);
+  if (h->aux_join) cudaEventDestroy(h->aux_join);
   cudaGetLastError();
   delete h;
 }
@@ -298,6 +304,12 @@ dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, co
   for (int m = 0; m < 3; ++m) {
     if ((st = dalloc(h, &h->F[m], elem_size(h->dtype) * (size_t)dims[m] * R)) != DFACTO_OK) return bail(st);
     if ((st = dalloc(h, (void**)&h->gram[m], sizeof(double) * RR)) != DFACTO_OK) return bail(st);
+  }
+  if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->aux_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->aux_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(DFACTO_ECUDA);
   }
   h->host_scal = new (std::nothrow) double[kNumScalars]();
   h->host_flags = new (std::nothrow) int32_t[kNumFlags]();

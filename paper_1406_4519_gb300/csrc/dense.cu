@@ -916,34 +916,115 @@ struct PassShape {
   static constexpr int NB4 = RT / 4, NBLK = NB4 * NB4, NGRP = kT / NBLK;
 };
 
-// Pass 1: colsq[vb][c] = sum over the block's rows of (N W)[row, c]^2.  Each
-// thread sums its rows in FP32; the block adds the threads in FP64, in thread
-// order.
+// Rows [t0, t0 + nt) of an R-column row-major matrix (one contiguous run of
+// nt * R floats) into tile rows of stride LD, with coalesced 16-byte loads when
+// R % 4 == 0.  Columns R .. RT-1 of the tile are left as they are (zero).
+template <int LD>
+__device__ __forceinline__ void tile_load(const float* __restrict__ M, int64_t t0, int nt, int R,
+                                          float* __restrict__ tile) {
+  const float* src = M + t0 * R;
+  const int total = nt * R;
+  if ((R & 3) == 0) {
+    for (int e4 = threadIdx.x; e4 < (total >> 2); e4 += kT) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(src) + e4);
+      const int e = 4 * e4, r = e / R, c = e - r * R;
+      *reinterpret_cast<float4*>(tile + r * LD + c) = v;
+    }
+  } else {
+    for (int e = threadIdx.x; e < total; e += kT) {
+      const int r = e / R, c = e - r * R;
+      tile[r * LD + c] = __ldg(src + e);
+    }
+  }
+}
+
+// Tile rows (already rounded to T) back to rows [t0, t0 + nt) of an R-column
+// matrix in storage type T, with coalesced 16-byte stores where the layout
+// allows (FP32: R % 4 == 0; BF16: R % 8 == 0).
+template <int LD>
+__device__ __forceinline__ void tile_store(const float* __restrict__ tile, int64_t t0, int nt, int R,
+                                           float* __restrict__ M) {
+  float* dst = M + t0 * R;
+  const int total = nt * R;
+  if ((R & 3) == 0) {
+    for (int e4 = threadIdx.x; e4 < (total >> 2); e4 += kT) {
+      const int e = 4 * e4, r = e / R, c = e - r * R;
+      reinterpret_cast<float4*>(dst)[e4] = *reinterpret_cast<const float4*>(tile + r * LD + c);
+    }
+  } else {
+    for (int e = threadIdx.x; e < total; e += kT) {
+      const int r = e / R, c = e - r * R;
+      dst[e] = tile[r * LD + c];
+    }
+  }
+}
+template <int LD>
+__device__ __forceinline__ void tile_store(const float* __restrict__ tile, int64_t t0, int nt, int R,
+                                           __nv_bfloat16* __restrict__ M) {
+  __nv_bfloat16* dst = M + t0 * R;
+  const int total = nt * R;
+  if ((R & 7) == 0) {
+    for (int e8 = threadIdx.x; e8 < (total >> 3); e8 += kT) {
+      const int e = 8 * e8, r = e / R, c = e - r * R;
+      const float* q = tile + r * LD + c;
+      uint4 w;
+      w.x = (__float_as_uint(q[0]) >> 16) | (__float_as_uint(q[1]) & 0xffff0000u);
+      w.y = (__float_as_uint(q[2]) >> 16) | (__float_as_uint(q[3]) & 0xffff0000u);
+      w.z = (__float_as_uint(q[4]) >> 16) | (__float_as_uint(q[5]) & 0xffff0000u);
+      w.w = (__float_as_uint(q[6]) >> 16) | (__float_as_uint(q[7]) & 0xffff0000u);
+      reinterpret_cast<uint4*>(dst)[e8] = w;  // values are BF16-exact: the high halves
+    }
+  } else {
+    for (int e = threadIdx.x; e < total; e += kT) {
+      const int r = e / R, c = e - r * R;
+      st_elem(dst + e, tile[r * LD + c]);
+    }
+  }
+}
+
+// Pass 1: colsq[vb][c] = sum over the block's rows of (N W)[row, c]^2.  A tile
+// of kT rows is loaded into shared memory with coalesced loads; thread t then
+// takes row t of the tile.  Each thread sums its rows in FP32; the block adds
+// the threads in FP64, in thread order.
 template <int RT>
 __device__ __forceinline__ void colnorm_rows_body(const float* __restrict__ N,
                                                   const float* __restrict__ W32, int64_t rows, int R,
                                                   double* __restrict__ colsq, int vb, int vgrid) {
-  constexpr int CW = PassShape<RT>::CW;
+  using PS = PassShape<RT>;
+  constexpr int CW = PS::CW, LD = PS::LD;
+  static_assert(LD >= RT + 1, "the tile doubles as the FP64 reduction area");
   __shared__ __align__(16) float Ws[RT * RT];
-  __shared__ float red[kT * (RT + 1)];
+  __shared__ __align__(16) float tile[kT * LD];
   stage_w<RT>(W32, R, Ws);
-  __syncthreads();
+  for (int e = threadIdx.x; e < kT * LD; e += kT) tile[e] = 0.f;
   int64_t r0, r1;
   block_rows(rows, vb, vgrid, r0, r1);
   float sq[RT];
 #pragma unroll
   for (int c = 0; c < RT; ++c) sq[c] = 0.f;
-  for (int64_t r = r0 + threadIdx.x; r < r1; r += kT) {
-    float n[RT];
-    load_row<RT>(N, r, R, n);
+  for (int64_t t0 = r0; t0 < r1; t0 += kT) {
+    const int nt = (int)min((int64_t)kT, r1 - t0);
+    __syncthreads();
+    tile_load<LD>(N, t0, nt, R, tile);
+    __syncthreads();
+    if ((int)threadIdx.x < nt) {
+      float n[RT];
 #pragma unroll
-    for (int h = 0; h < RT / CW; ++h) {
-      float o[CW];
-      row_solve<RT, CW>(n, Ws, h * CW, o);
+      for (int c4 = 0; c4 < RT / 4; ++c4) {
+        const float4 v = *reinterpret_cast<const float4*>(tile + threadIdx.x * LD + 4 * c4);
+        n[4 * c4] = v.x; n[4 * c4 + 1] = v.y; n[4 * c4 + 2] = v.z; n[4 * c4 + 3] = v.w;
+      }
 #pragma unroll
-      for (int c = 0; c < CW; ++c) sq[h * CW + c] = fmaf(o[c], o[c], sq[h * CW + c]);
+      for (int h = 0; h < RT / CW; ++h) {
+        float o[CW];
+        row_solve<RT, CW>(n, Ws, h * CW, o);
+#pragma unroll
+        for (int c = 0; c < CW; ++c) sq[h * CW + c] = fmaf(o[c], o[c], sq[h * CW + c]);
+      }
     }
   }
+  __syncthreads();
+  float* red = tile;  // [kT][RT + 1]
 #pragma unroll
   for (int c = 0; c < RT; ++c) red[threadIdx.x * (RT + 1) + c] = sq[c];
   __syncthreads();
@@ -955,11 +1036,13 @@ __device__ __forceinline__ void colnorm_rows_body(const float* __restrict__ N,
 }
 
 // Pass 2: F[row] = (N W)[row] * inv stored in T; Gram partials of the stored
-// values gpart[vb][R*R]: a tile of kT rows at a time goes through shared
-// memory and thread (grp, blk) adds the outer products of the 4 x 4 block blk
-// over rows grp, grp + NGRP, ... in FP32; the groups are added in FP64, in
-// group order.  With with_ip also ipart[vb] = sum lambda_c F_stored[row, c]
-// N[row, c] (the fit's inner product after the last mode).
+// values gpart[vb][R*R]: a tile of kT rows is loaded into shared memory with
+// coalesced loads, thread t replaces row t of the tile by its stored values,
+// the tile is written to F with coalesced stores, and thread (grp, blk) adds
+// the outer products of the 4 x 4 block blk over rows grp, grp + NGRP, ... in
+// FP32; the groups are added in FP64, in group order.  With with_ip also
+// ipart[vb] = sum lambda_c F_stored[row, c] N[row, c] (the fit's inner
+// product after the last mode).
 template <typename T, int RT>
 __device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ N,
                                                       const float* __restrict__ W32,
@@ -979,6 +1062,7 @@ __device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ 
     s_sc[c] = c < R ? inv[c] : 0.f;
     s_lm[c] = (with_ip && c < R) ? (float)lambda[c] : 0.f;
   }
+  for (int e = threadIdx.x; e < kT * LD; e += kT) tile[e] = 0.f;
   const int blk = threadIdx.x % NBLK, grp = threadIdx.x / NBLK;
   const int bi = blk / NB4, bj = blk % NB4;
   float a32[16];
@@ -987,15 +1071,20 @@ __device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ 
   double ip = 0.0;
   int64_t r0, r1;
   block_rows(rows, vb, vgrid, r0, r1);
-  __syncthreads();
   for (int64_t t0 = r0; t0 < r1; t0 += kT) {
-    const int64_t r = t0 + threadIdx.x;
+    const int nt = (int)min((int64_t)kT, r1 - t0);
+    __syncthreads();
+    tile_load<LD>(N, t0, nt, R, tile);
+    __syncthreads();
     float ip32 = 0.f;
     float* trow = tile + threadIdx.x * LD;
-    if (r < r1) {
+    if ((int)threadIdx.x < nt) {
       float n[RT];
-      load_row<RT>(N, r, R, n);
-      T* frow = F + r * R;
+#pragma unroll
+      for (int c4 = 0; c4 < RT / 4; ++c4) {
+        const float4 v = *reinterpret_cast<const float4*>(trow + 4 * c4);
+        n[4 * c4] = v.x; n[4 * c4 + 1] = v.y; n[4 * c4 + 2] = v.z; n[4 * c4 + 3] = v.w;
+      }
 #pragma unroll
       for (int h = 0; h < RT / CW; ++h) {
         float o[CW];
@@ -1005,7 +1094,6 @@ __device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ 
           const int col = h * CW + c;
           const float x = o[c] * s_sc[col];
           const float v = col < R ? rt_elem(F, x) : 0.f;
-          if (col < R) st_elem(frow + col, x);
           ip32 = fmaf(s_lm[col] * v, n[col], ip32);
           o[c] = v;
         }
@@ -1021,7 +1109,7 @@ __device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ 
     }
     ip += (double)ip32;
     __syncthreads();
-    const int nt = (int)min((int64_t)kT, r1 - t0);
+    tile_store<LD>(tile, t0, nt, R, F);
     for (int i = grp; i < nt; i += NGRP) {
       const float4 xv = *reinterpret_cast<const float4*>(tile + i * LD + 4 * bi);
       const float4 yv = *reinterpret_cast<const float4*>(tile + i * LD + 4 * bj);
@@ -1031,7 +1119,6 @@ __device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ 
 #pragma unroll
         for (int w = 0; w < 4; ++w) a32[u * 4 + w] = fmaf(xa[u], ya[w], a32[u * 4 + w]);
     }
-    __syncthreads();
   }
   if (with_ip) {
     const double t = block_sum(ip, red);
@@ -1039,6 +1126,7 @@ __device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ 
   }
   // Add the groups of each block in group order, four entries at a time
   // through the tile ([kT][4] doubles = 8 KB <= the tile's kT * LD floats).
+  __syncthreads();
   double* rsm = reinterpret_cast<double*>(tile);
   for (int q0 = 0; q0 < 16; q0 += 4) {
 #pragma unroll
@@ -1311,9 +1399,26 @@ dfacto_status als_post(dfacto_t* h, int mode, float* N) {
   return h->dtype == DFACTO_BF16 ? als_post_T<__nv_bfloat16>(h, mode, N) : als_post_T<float>(h, mode, N);
 }
 
+// One mode of Algorithm 2.  Gamma^{-1} depends only on the other two factors,
+// so it runs on the handle's auxiliary stream beside the MTTKRP; the row
+// passes wait for both.
 dfacto_status als_mode(dfacto_t* h, int mode) {
-  dfacto_status st = als_pre(h, mode);
-  if (st == DFACTO_OK) st = mttkrp_launch(h, mode, h->N);
+  dfacto_status st;
+  if (h->aux) {
+    DF_CUDA(h, cudaEventRecord(h->aux_fork, h->stream));
+    DF_CUDA(h, cudaStreamWaitEvent(h->aux, h->aux_fork, 0));
+    cudaStream_t main = h->stream;
+    h->stream = h->aux;
+    st = als_pre(h, mode);
+    h->stream = main;
+    cudaError_t e = cudaEventRecord(h->aux_join, h->aux);
+    if (st == DFACTO_OK) st = mttkrp_launch(h, mode, h->N);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->aux_join, 0);
+    if (e != cudaSuccess && st == DFACTO_OK) return cuda_fail(h, e, "auxiliary stream join");
+  } else {
+    st = als_pre(h, mode);
+    if (st == DFACTO_OK) st = mttkrp_launch(h, mode, h->N);
+  }
   if (st == DFACTO_OK) st = als_post(h, mode, h->N);
   return st;
 }

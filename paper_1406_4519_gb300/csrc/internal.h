@@ -70,6 +70,9 @@ enum Flag : int {
 
 struct dfacto_handle {
   cudaStream_t stream = nullptr;
+  cudaStream_t aux = nullptr;        // Gamma^{-1} beside the MTTKRP (created at build)
+  cudaEvent_t aux_fork = nullptr;
+  cudaEvent_t aux_join = nullptr;
   int device = 0;
   int32_t dims[3] = {0, 0, 0};
   int64_t nnz = 0;
