@@ -213,6 +213,16 @@ def emit(obj):
     print(json.dumps(obj), flush=True)
 
 
+def max_over_ranks_of(x: float, world: int, device) -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself at N = 1."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
@@ -282,11 +292,7 @@ def run_ours(args, rank, world, local_rank):
             torch.distributed.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(x, world, dev)
 
     # -- input (seeded, synthetic, generated on the device) --------------------
     if wl["zipf"]:
