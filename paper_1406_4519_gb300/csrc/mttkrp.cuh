@@ -389,6 +389,41 @@ __global__ void __launch_bounds__(kWalkWarps * 32) mttkrp_walk(const MttkrpParam
 // The merge of rows shared between segments, warps and CTAs is the one of
 // mttkrp_walk.
 // ---------------------------------------------------------------------------
+// VEC consecutive floats in shared memory, one vector access where VEC allows.
+template <int VEC>
+__device__ __forceinline__ void smem_st(float* p, const float (&v)[VEC]) {
+  if constexpr (VEC % 4 == 0) {
+#pragma unroll
+    for (int e = 0; e < VEC; e += 4)
+      *reinterpret_cast<float4*>(p + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+  } else if constexpr (VEC == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) p[e] = v[e];
+  }
+}
+template <int VEC>
+__device__ __forceinline__ void smem_ld(const float* p, float (&v)[VEC]) {
+  if constexpr (VEC % 4 == 0) {
+#pragma unroll
+    for (int e = 0; e < VEC; e += 4) {
+      const float4 t = *reinterpret_cast<const float4*>(p + e);
+      v[e] = t.x; v[e + 1] = t.y; v[e + 2] = t.z; v[e + 3] = t.w;
+    }
+  } else if constexpr (VEC == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) v[e] = p[e];
+  }
+}
+
+// Fibers closed per round of the fiber-closing pass (fewer predicated-off
+// slots when fibers are long; a sub-batch closes at most U).
+constexpr int kCloseChunk = 4;
+
 template <typename T, int VEC, int G>
 struct Walk2Shape {
   static constexpr int NG = 32 / G;
@@ -416,7 +451,7 @@ __device__ __forceinline__ void walk2_cta(const MttkrpParams& a, int cta, float*
   const int R = a.R;
   float* s_val = smem;                           // [SEGS * 2][R]
   float* w_val = smem + (size_t)SEGS * 2 * R;    // [kWalkWarps * 2][R]
-  float* vb = w_val + (size_t)kWalkWarps * 2 * R;  // [U][VEC][NT] parked fiber sums
+  float* vb = w_val + (size_t)kWalkWarps * 2 * R;  // [U][NT][VEC] parked fiber sums
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -474,8 +509,10 @@ __device__ __forceinline__ void walk2_cta(const MttkrpParams& a, int cta, float*
     const bool okl = pl < p1;
     const int my_in = okl ? __ldg(a.nz_idx + pl) : 0;
     const float my_x = okl ? __ldg(a.nz_val + pl) : 0.f;
-    // end bits of the batch's G positions (base is a multiple of G, G | 32)
-    const uint32_t ebits = active ? (__ldg(a.end_bits + (base >> 5)) >> (base & 31)) : 0u;
+    // end bits of the batch's G positions (base is a multiple of G, G | 32);
+    // a batch starting at or past p1 has none, and its word may lie past the
+    // end of end_bits ((nnz + 31) / 32 words) in the last segment
+    const uint32_t ebits = (active && base < p1) ? (__ldg(a.end_bits + (base >> 5)) >> (base & 31)) : 0u;
 #pragma unroll
     for (int u0 = 0; u0 < G; u0 += U) {
       float fin[U][VEC];
@@ -498,30 +535,30 @@ __device__ __forceinline__ void walk2_cta(const MttkrpParams& a, int cta, float*
         for (int e = 0; e < VEC; ++e) v[e] = fmaf(x, fin[uu][e], v[e]);
         const bool end = p < p1 && ((ebits >> (u0 + uu)) & 1u);
         if (end) {
+          smem_st<VEC>(vb + ((size_t)k * NT + tid) * VEC, v);
 #pragma unroll
-          for (int e = 0; e < VEC; ++e) {
-            vb[((size_t)k * VEC + e) * NT + tid] = v[e];
-            v[e] = 0.f;
-          }
+          for (int e = 0; e < VEC; ++e) v[e] = 0.f;
         }
         k += end ? 1 : 0;
       }
-      // Close the k fibers q .. q + k - 1.
-      if (k > 0) {
-        int fj[U], rj[U];
+      // Close the k fibers q .. q + k - 1, CC at a time (the F_f gathers of a
+      // round are issued together).
+      constexpr int CC = kCloseChunk < U ? kCloseChunk : U;
+      for (int j0 = 0; j0 < k; j0 += CC) {
+        int fj[CC], rj[CC];
 #pragma unroll
-        for (int j = 0; j < U; ++j) {
+        for (int j = 0; j < CC; ++j) {
           fj[j] = 0;
           rj[j] = row_cur;
-          if (j < k) {
-            fj[j] = __ldg(a.fiber_idx + q + j);
-            rj[j] = __ldg(a.fiber_row + q + j);
+          if (j0 + j < k) {
+            fj[j] = __ldg(a.fiber_idx + q + j0 + j);
+            rj[j] = __ldg(a.fiber_row + q + j0 + j);
           }
         }
-        float ff[U][VEC];
+        float ff[CC][VEC];
 #pragma unroll
-        for (int j = 0; j < U; ++j) {
-          if (j < k && colok) {
+        for (int j = 0; j < CC; ++j) {
+          if (j0 + j < k && colok) {
             VecIO<T, VEC>::load(Ff + (int64_t)fj[j] * R + col0, ff[j]);
           } else {
 #pragma unroll
@@ -529,16 +566,15 @@ __device__ __forceinline__ void walk2_cta(const MttkrpParams& a, int cta, float*
           }
         }
 #pragma unroll
-        for (int j = 0; j < U; ++j) {
-          if (j < k) {
+        for (int j = 0; j < CC; ++j) {
+          if (j0 + j < k) {
             float vv[VEC];
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) vv[e] = vb[((size_t)j * VEC + e) * NT + tid];
+            smem_ld<VEC>(vb + ((size_t)(j0 + j) * NT + tid) * VEC, vv);
             fold(rj[j], vv, ff[j]);
           }
         }
-        q += k;
       }
+      q += k;
     }
   }
   // The fiber open at the segment end (if its last nonzero lies beyond p1).
