@@ -58,10 +58,10 @@ BATCH_WORKLOADS = {
 # Serving: Poisson arrivals of jobs shaped like the batch workload's, served
 # to |fit change| < 1e-4 or 50 sweeps with BF16 factors under a 120 GB budget.
 SERVE_WORKLOADS = {
-    "serve2000": dict(desc="2000 requests, Poisson(50/s) arrivals, job shapes as batch256 with "
-                           "planted rank-R CP values + 1% noise, BF16 factors, until |fit change| "
-                           "< 1e-4 or 50 sweeps, 120 GB budget",
-                      n_req=2000, rate=50.0, seed=14064524, budget=120e9, baseline_req=300,
+    "serve2000": dict(desc="2000 requests, Poisson(50/s) arrivals, jobs drawn as batch256 (uniform "
+                           "coordinates, U(0,1) values, R in {8,16,32}), BF16 factors, until "
+                           "relative fit change < 1e-4 or 50 sweeps, 120 GB budget",
+                      n_req=2000, rate=50.0, seed=14064524, budget=120e9, cmp_req=500,
                       burst_req=500),
 }
 CPU_PHI = 0.1              # cpu_baseline: replica scaled by this factor (~10-30 s)
@@ -542,10 +542,11 @@ def run_batch(args, rank, world, local_rank):
 
 def run_serve(args, rank, world, local_rank):
     """Requests arrive on a Poisson clock; the server admits, batches and
-    retires them in real time.  value = finished jobs per second; also the
-    p50 / p99 latency from arrival to factors on the host, and the same for a
-    server that runs one job at a time with FP32 ALS (on the first
-    baseline_req arrivals)."""
+    retires them in real time.  value = finished jobs per second over all
+    requests, with the p50 / p99 latency from arrival to factors on the host.
+    Beside it, on the first cmp_req arrivals, the same server and a server that
+    runs one job at a time with FP32 ALS (jobs/s, latency, final fit), and both
+    servers on a burst of burst_req requests arriving at once."""
     import torch
 
     from paper_1406_4519_gb300 import dfacto, serve, synth
@@ -555,12 +556,10 @@ def run_serve(args, rank, world, local_rank):
     specs = synth.batch_job_specs(wl["n_req"], wl["seed"])
     arrivals = synth.poisson_arrivals(wl["n_req"], wl["rate"], wl["seed"] + 1)
     # Inputs generated before the clock starts (as if received into device
-    # memory at arrival): uniform coordinates (Zipf exponent 0), values from a
-    # planted rank-R CP model plus 1% noise.
+    # memory at arrival).
     data = []
     for sp in specs:
-        idx, val = synth.zipf_tensor(sp["dims"], sp["nnz"], [0.0, 0.0, 0.0], seed=sp["seed"],
-                                     device=dev, values="cp", R_true=sp["R"])
+        idx, val = synth.uniform_tensor(sp["dims"], sp["nnz"], seed=sp["seed"], device=dev)
         F0 = synth.normal_factors(sp["dims"], sp["R"], seed=sp["seed"] + 1, device=dev)
         data.append((idx, val, F0))
     torch.cuda.synchronize()
@@ -569,25 +568,27 @@ def run_serve(args, rank, world, local_rank):
         return [serve.JobSpec(i, 0.0 if burst else arrivals[i], specs[i]["dims"], specs[i]["nnz"],
                               specs[i]["R"], make=(lambda i=i: data[i])) for i in range(n)]
 
+    def batched(jobs):
+        return serve.latency_stats(serve.serve(jobs, budget_bytes=wl["budget"], max_iters=50,
+                                               tol=1e-4, factor_dtype=dfacto.BF16))
+
+    def sequential(jobs):
+        return serve.latency_stats(serve.serve_sequential(jobs, max_iters=50, tol=1e-4,
+                                                          factor_dtype=dfacto.F32))
+
     launches0 = dfacto.dfacto_launch_count()
     sampler = ClockSampler(local_rank)
     sampler.start()
-    done = serve.serve(jobs_of(wl["n_req"]), budget_bytes=wl["budget"], max_iters=50, tol=1e-4,
-                       factor_dtype=dfacto.BF16)
+    st = batched(jobs_of(wl["n_req"]))
     sampler.stop()
     launches = dfacto.dfacto_launch_count() - launches0
-    st = serve.latency_stats(done)
-    nb = min(wl["baseline_req"], wl["n_req"])
-    base = serve.latency_stats(serve.serve_sequential(jobs_of(nb), max_iters=50, tol=1e-4,
-                                                      factor_dtype=dfacto.F32))
-    # Saturation: burst_req requests all at time 0.
+    nc = min(wl["cmp_req"], wl["n_req"])
+    cmp_b, cmp_s = batched(jobs_of(nc)), sequential(jobs_of(nc))
     nbu = min(wl["burst_req"], wl["n_req"])
-    burst = serve.latency_stats(serve.serve(jobs_of(nbu, burst=True), budget_bytes=wl["budget"],
-                                            max_iters=50, tol=1e-4, factor_dtype=dfacto.BF16))
-    burst_seq = serve.latency_stats(serve.serve_sequential(jobs_of(nbu, burst=True), max_iters=50,
-                                                           tol=1e-4, factor_dtype=dfacto.F32))
+    bur_b, bur_s = batched(jobs_of(nbu, burst=True)), sequential(jobs_of(nbu, burst=True))
     if rank != 0:
         return
+    keep = ("jobs_per_s", "p50_s", "p99_s", "mean_s", "mean_iters", "mean_final_fit")
     emit({
         "metric": "jobs/s", "value": world * st["jobs_per_s"], "unit": "jobs/s", "n_gpus": world,
         "steps": st["jobs"], "warmup": 0, "ms_per_step": 1e3 / st["jobs_per_s"],
@@ -598,11 +599,11 @@ def run_serve(args, rank, world, local_rank):
                          "exceeds the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "latency": {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
-                    "mean_sweeps": st["mean_iters"]},
-        "sequential_fp32": dict(base, requests=nb),
-        "burst": {"requests": nbu, "batched_jobs_per_s": burst["jobs_per_s"],
-                  "batched_p99_s": burst["p99_s"], "sequential_fp32_jobs_per_s": burst_seq["jobs_per_s"],
-                  "sequential_fp32_p99_s": burst_seq["p99_s"]},
+                    "mean_sweeps": st["mean_iters"], "mean_final_fit": st["mean_final_fit"]},
+        "same_requests": {"requests": nc, "batched_bf16": {k: cmp_b[k] for k in keep},
+                          "sequential_fp32": {k: cmp_s[k] for k in keep}},
+        "burst": {"requests": nbu, "batched_bf16": {k: bur_b[k] for k in keep},
+                  "sequential_fp32": {k: bur_s[k] for k in keep}},
         "gpu_launches": launches, "clocks": sampler.summary(),
     })
 

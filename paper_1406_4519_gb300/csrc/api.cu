@@ -231,7 +231,7 @@ void dfacto_destroy(dfacto_t* h) {
       if (q) cudaFreeAsync(q, h->stream);
   }
   for (void* q : {(void*)h->N, (void*)h->Fh, (void*)h->lambda, (void*)h->inv_lambda, (void*)h->ipart,
-                  (void*)h->gd_mats, (void*)h->W, (void*)h->rr_work, (void*)h->W32, (void*)h->scal,
+                  (void*)h->gd_mats, (void*)h->gd_scratch, (void*)h->W, (void*)h->rr_work, (void*)h->W32, (void*)h->scal,
                   (void*)h->flags, (void*)h->partials, (void*)h->carry, (void*)h->carry_row})
     if (q) cudaFreeAsync(q, h->stream);
   delete[] h->host_scal;
@@ -295,6 +295,7 @@ dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, co
   if ((st = dalloc(h, (void**)&h->inv_lambda, sizeof(float) * R)) != DFACTO_OK) return bail(st);
   if ((st = dalloc(h, (void**)&h->ipart, sizeof(double) * 608 * R)) != DFACTO_OK) return bail(st);  // >= blocks
   if ((st = dalloc(h, (void**)&h->gd_mats, sizeof(double) * 9 * RR)) != DFACTO_OK) return bail(st);
+  if ((st = dalloc(h, (void**)&h->gd_scratch, sizeof(uint32_t) * 8)) != DFACTO_OK) return bail(st);
   if ((st = dalloc(h, (void**)&h->W, sizeof(double) * RR)) != DFACTO_OK) return bail(st);
   if ((st = dalloc(h, (void**)&h->rr_work, sizeof(double) * (2 * RR + R))) != DFACTO_OK) return bail(st);
   if ((st = dalloc(h, (void**)&h->W32, sizeof(float) * RR)) != DFACTO_OK) return bail(st);

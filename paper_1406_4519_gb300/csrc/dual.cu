@@ -9,6 +9,13 @@
 // T101 += GA[i,:].u2, T011 += A[i,:].u3, T111 += GA[i,:].u3.  Only scalars
 // leave the walk, so rows split between segments need no carries.  Segment sums
 // are FP32 (at most one segment of nonzeros), everything above is FP64.
+//
+// Range: T111 carries three gradient factors, and gradients reach 1e13 and
+// more on large tensors (|F Gamma| grows with the product of two dimensions),
+// so x * g^3 would overflow FP32.  Each gradient is therefore read scaled by
+// 2^-e_n, its largest magnitude brought into [0.5, 1); the terms are divided
+// by the product of their scales in FP64.  Powers of two scale exactly, so the
+// result is the unscaled arithmetic wherever that did not overflow.
 #include <algorithm>
 
 #include "device.cuh"
@@ -30,6 +37,7 @@ struct DualParams {
   const float* GA;
   const float* GB;
   const float* GC;
+  const float* gscale;  // [3] power-of-two scales of GA, GB, GC
   double* part;  // [ncta][4]
   int64_t nnz;
   int64_t nfib;
@@ -56,6 +64,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) dual_walk(const DualParams a)
   const T* B = static_cast<const T*>(a.B);
   const T* C = static_cast<const T*>(a.C);
 
+  const float sA = a.gscale[0], sB = a.gscale[1], sC = a.gscale[2];
   float vB[VEC], vG[VEC], cf[VEC], gcf[VEC], u1[VEC], u2[VEC], u3[VEC];
 #pragma unroll
   for (int q = 0; q < VEC; ++q) vB[q] = vG[q] = cf[q] = gcf[q] = u1[q] = u2[q] = u3[q] = 0.f;
@@ -70,6 +79,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32) dual_walk(const DualParams a)
     if (colok) {
       VecIO<T, VEC>::load(C + (int64_t)k * R + col0, cf);
       VecIO<float, VEC>::load(a.GC + (int64_t)k * R + col0, gcf);
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) gcf[q] *= sC;
     }
   };
   auto emit_row = [&]() {
@@ -77,6 +88,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32) dual_walk(const DualParams a)
     float ar[VEC], gar[VEC];
     VecIO<T, VEC>::load(A + (int64_t)row_cur * R + col0, ar);
     VecIO<float, VEC>::load(a.GA + (int64_t)row_cur * R + col0, gar);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) gar[q] *= sA;
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
       t[0] = fmaf(gar[q], u1[q], t[0]);
@@ -105,6 +118,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32) dual_walk(const DualParams a)
           float b[VEC], gb[VEC];
           VecIO<T, VEC>::load(B + (int64_t)j * R + col0, b);
           VecIO<float, VEC>::load(a.GB + (int64_t)j * R + col0, gb);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) gb[q] *= sB;
 #pragma unroll
           for (int q = 0; q < VEC; ++q) {
             vB[q] = fmaf(x, b[q], vB[q]);
@@ -148,10 +163,14 @@ __global__ void __launch_bounds__(kWalkWarps * 32) dual_walk(const DualParams a)
 }
 
 // scal[kT110 + k] = sum over CTAs of part[b][k], k = 0..3 (fixed order:
-// strided per-thread sums, then a fixed tree).
+// strided per-thread sums, then a fixed tree), divided by the term's scales.
 __global__ void __launch_bounds__(256) dual_reduce(const double* __restrict__ part, int64_t ncta,
+                                                   const float* __restrict__ gscale,
                                                    double* __restrict__ scal) {
   __shared__ double red[256];
+  const double sA = gscale[0], sB = gscale[1], sC = gscale[2];
+  const double unscale[4] = {1.0 / (sA * sB), 1.0 / (sA * sC), 1.0 / (sB * sC),
+                             1.0 / (sA * sB * sC)};
   for (int k = 0; k < 4; ++k) {
     double v = 0.0;
     for (int64_t b = threadIdx.x; b < ncta; b += 256) v += part[b * 4 + k];
@@ -161,9 +180,36 @@ __global__ void __launch_bounds__(256) dual_reduce(const double* __restrict__ pa
       if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
       __syncthreads();
     }
-    if (threadIdx.x == 0) scal[kT110 + k] = red[0];
+    if (threadIdx.x == 0) scal[kT110 + k] = red[0] * unscale[k];
     __syncthreads();
   }
+}
+
+// Largest |g| of each gradient (as ordered bits of a non-negative float;
+// atomicMax keeps it independent of the order), then scale[n] = 2^-e with
+// max = m 2^e, m in [0.5, 1) (1 when the gradient is zero or not finite).
+__global__ void grad_absmax(const float* __restrict__ g, int64_t n, unsigned* __restrict__ out) {
+  unsigned m = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    m = max(m, __float_as_uint(fabsf(g[i])));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__global__ void grad_scales(const unsigned* __restrict__ maxbits, float* __restrict__ scale) {
+  const int n = threadIdx.x;
+  if (n >= 3) return;
+  const float m = __uint_as_float(maxbits[n]);
+  float sc = 1.f;
+  if (m > 0.f && isfinite(m)) {
+    int e;
+    frexpf(m, &e);        // m = f 2^e, f in [0.5, 1)
+    sc = ldexpf(1.f, -e);  // 2^-e, exact
+    if (sc == 0.f || !isfinite(sc)) sc = 1.f;
+  }
+  scale[n] = sc;
 }
 
 template <typename T, int VEC, int G>
@@ -195,6 +241,16 @@ dfacto_status dual_pass(dfacto_t* h) {
   const int64_t P = (int64_t)segs * cfg.seg;
   const int64_t ncta = (h->nnz + P - 1) / P;
   if ((st = grow_partials(h, ncta * 4)) != DFACTO_OK) return st;
+  // Scales of the three gradients.
+  unsigned* maxbits = h->gd_scratch;
+  float* gscale = reinterpret_cast<float*>(h->gd_scratch + 4);
+  DF_CUDA(h, cudaMemsetAsync(maxbits, 0, 3 * sizeof(unsigned), h->stream));
+  for (int m = 0; m < 3; ++m) {
+    const int64_t n = (int64_t)h->dims[m] * h->R;
+    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+    grad_absmax<<<nb, 256, 0, h->stream>>>(h->grad[m], n, maxbits + m); DF_COUNT();
+  }
+  grad_scales<<<1, 32, 0, h->stream>>>(maxbits, gscale); DF_COUNT();
   if (ncta == 0) {
     DF_CUDA(h, cudaMemsetAsync(h->scal + kT110, 0, 4 * sizeof(double), h->stream));
     return DFACTO_OK;
@@ -212,6 +268,7 @@ dfacto_status dual_pass(dfacto_t* h) {
   a.GA = h->grad[0];
   a.GB = h->grad[1];
   a.GC = h->grad[2];
+  a.gscale = gscale;
   a.part = h->partials;
   a.nnz = h->nnz;
   a.nfib = M.nfib;
@@ -221,7 +278,7 @@ dfacto_status dual_pass(dfacto_t* h) {
                       ? launch<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, h->stream)
                       : launch<float>(cfg.vec, cfg.G, a, ncta, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "dual_walk launch");
-  dual_reduce<<<1, 256, 0, h->stream>>>(h->partials, ncta, h->scal); DF_COUNT();
+  dual_reduce<<<1, 256, 0, h->stream>>>(h->partials, ncta, gscale, h->scal); DF_COUNT();
   DF_CUDA(h, cudaGetLastError());
   return DFACTO_OK;
 }

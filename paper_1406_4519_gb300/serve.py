@@ -4,14 +4,18 @@ Jobs (sparse 3-way tensors with a rank) arrive over time.  The server keeps
 every admitted job resident on the GPU (its flattened CSR copies and factors),
 advances all admitted jobs together one ALS sweep (Algorithm 4) at a time
 through a batch (dfacto_batch_*), and retires a job when its fit stops moving
-(|fit - previous fit| < tol) or after max_iters sweeps; the job's result is its
-factors and weights, copied to the host at retirement.
+(relative change |fit - previous fit| < tol |previous fit|, or absolute with
+relative=False) or after max_iters sweeps; the job's result is its factors and
+weights, copied to the host at retirement.
 
 Admission is first come, first served under a device-memory budget: a job is
 admitted when the estimated footprint of everything admitted stays within the
-budget.  Membership changes (admissions, retirements) take effect when the
-batch is rebuilt, at most once per `rebuild_interval` seconds, so that a burst
-of arrivals does not rebuild the batch after every sweep.
+budget.  Membership changes take effect when the batch is rebuilt (its
+concatenated CSR copies are rebuilt from the jobs', a cost that grows with
+everything resident): admissions at most once per `rebuild_interval` seconds,
+so that a burst of arrivals does not rebuild after every sweep; retirements
+alone only once the finished jobs, which ride along until then, hold
+`waste_limit` of the batch's nonzeros.
 
 The scheduling decisions live in `Scheduler` (pure Python, no GPU), the device
 work in `GpuEngine`; `serve()` runs the loop in real time against a list of
@@ -66,14 +70,26 @@ def footprint_bytes(dims: Sequence[int], nnz: int, rank: int, factor_bytes: int)
     return 2 * csr + 2 * factors + rows + (1 << 20)
 
 
+def converged(fits: Sequence[float], tol: float, relative: bool = True) -> bool:
+    """|fit_k - fit_{k-1}| < tol * |fit_{k-1}| (relative) or < tol (absolute),
+    tested from the second sweep on."""
+    if len(fits) < 2:
+        return False
+    change = abs(fits[-1] - fits[-2])
+    return change < (tol * abs(fits[-2]) if relative else tol)
+
+
 class Scheduler:
     """Admission, retirement and rebuild decisions; no device work."""
 
     def __init__(self, budget_bytes: float, max_iters: int = 50, tol: float = 1e-4,
-                 rebuild_interval: float = 0.005, factor_bytes: int = 2):
+                 rebuild_interval: float = 0.005, factor_bytes: int = 2, relative: bool = True,
+                 waste_limit: float = 0.5):
         self.budget = float(budget_bytes)
         self.max_iters = int(max_iters)
         self.tol = float(tol)
+        self.relative = bool(relative)
+        self.waste_limit = float(waste_limit)
         self.rebuild_interval = float(rebuild_interval)
         self.factor_bytes = int(factor_bytes)
         self.pending: List[JobState] = []    # arrived, not admitted (FIFO)
@@ -109,14 +125,13 @@ class Scheduler:
 
     def record_sweep(self, fits: Dict[int, float]) -> List[JobState]:
         """Record one sweep's fits; return the jobs that are now finished
-        (|fit change| < tol, or max_iters sweeps)."""
+        (fit change below tolerance, or max_iters sweeps)."""
         finished = []
         for jid, fit in fits.items():
             job = self.active[jid]
             job.iters += 1
             job.fits.append(float(fit))
-            converged = len(job.fits) >= 2 and abs(job.fits[-1] - job.fits[-2]) < self.tol
-            if converged or job.iters >= self.max_iters:
+            if converged(job.fits, self.tol, self.relative) or job.iters >= self.max_iters:
                 finished.append(job)
         return finished
 
@@ -126,12 +141,17 @@ class Scheduler:
         self.used -= job.footprint
         self.done.append(job)
 
-    def should_rebuild(self, now: float, membership_changed: bool, have_batch: bool) -> bool:
-        if not membership_changed:
-            return False
+    def should_rebuild(self, now: float, admitted_waiting: bool, waste: float,
+                       have_batch: bool) -> bool:
+        """admitted_waiting: admitted jobs not yet in the batch; waste: the
+        fraction of the batch's nonzeros that belong to finished jobs."""
         if not have_batch:
+            return admitted_waiting
+        if not self.active:
+            return True  # everything in the batch has finished
+        if admitted_waiting and now - self.last_rebuild >= self.rebuild_interval:
             return True
-        return now - self.last_rebuild >= self.rebuild_interval
+        return waste >= self.waste_limit
 
 
 class GpuEngine:
@@ -189,19 +209,21 @@ class GpuEngine:
 def serve(jobs: Sequence[JobSpec], budget_bytes: float = 120e9, max_iters: int = 50,
           tol: float = 1e-4, rebuild_interval: float = 0.005, factor_dtype: Optional[int] = None,
           engine=None, clock: Callable[[], float] = time.perf_counter,
-          sleep: Callable[[float], None] = time.sleep) -> List[JobState]:
+          sleep: Callable[[float], None] = time.sleep, relative: bool = True) -> List[JobState]:
     """Serve `jobs` (sorted by arrival) in real time; returns the finished jobs
     with their latencies (arrival -> factors on the host)."""
     if engine is None:
         from . import dfacto
         engine = GpuEngine(dfacto.BF16 if factor_dtype is None else factor_dtype)
     fbytes = 4 if factor_dtype == 0 else 2
-    sch = Scheduler(budget_bytes, max_iters, tol, rebuild_interval, fbytes)
+    sch = Scheduler(budget_bytes, max_iters, tol, rebuild_interval, fbytes, relative)
     order = sorted(jobs, key=lambda j: j.arrival)
     nxt = 0
+    sch_done_nnz: Dict[int, int] = {}
     t0 = clock()
     retired_in_batch = set()   # finished jobs whose handles still sit in the batch
-    changed = False
+    in_batch_nnz = 0           # nonzeros of the jobs in the current batch
+    changed = False            # admitted jobs not yet in the batch
     while nxt < len(order) or sch.pending or sch.active:
         now = clock() - t0
         while nxt < len(order) and order[nxt].arrival <= now:
@@ -214,11 +236,15 @@ def serve(jobs: Sequence[JobSpec], budget_bytes: float = 120e9, max_iters: int =
             sch.admit(adm, clock() - t0)
             changed = True
         now = clock() - t0
-        if sch.should_rebuild(now, changed or bool(retired_in_batch), engine.batch is not None):
-            engine.rebuild(sorted(sch.active))
+        waste = (sum(sch_done_nnz[j] for j in retired_in_batch) / in_batch_nnz
+                 if in_batch_nnz else 0.0)
+        if sch.should_rebuild(now, changed, waste, engine.batch is not None):
+            members = sorted(sch.active)
+            engine.rebuild(members)
             for jid in retired_in_batch:
                 engine.release(jid)
             retired_in_batch.clear()
+            in_batch_nnz = sum(sch.active[j].spec.nnz for j in members)
             sch.last_rebuild = now
             changed = False
         if engine.batch is None or not sch.active:
@@ -231,13 +257,15 @@ def serve(jobs: Sequence[JobSpec], budget_bytes: float = 120e9, max_iters: int =
             job.result = engine.result(job.spec.job_id)
             sch.retire(job, clock() - t0)
             retired_in_batch.add(job.spec.job_id)
+            sch_done_nnz[job.spec.job_id] = job.spec.nnz
     engine.close()
     return sch.done
 
 
 def serve_sequential(jobs: Sequence[JobSpec], max_iters: int = 50, tol: float = 1e-4,
                      factor_dtype: int = 0, clock: Callable[[], float] = time.perf_counter,
-                     sleep: Callable[[float], None] = time.sleep) -> List[JobState]:
+                     sleep: Callable[[float], None] = time.sleep,
+                     relative: bool = True) -> List[JobState]:
     """The comparison server: one job at a time in arrival order, each run to
     convergence with the single-tensor ALS entry point."""
     import torch
@@ -258,7 +286,7 @@ def serve_sequential(jobs: Sequence[JobSpec], max_iters: int = 50, tol: float = 
             st, fit = t.als_iter(want_fit=True)
             job.iters += 1
             job.fits.append(fit)
-            if (len(job.fits) >= 2 and abs(job.fits[-1] - job.fits[-2]) < tol) or job.iters >= max_iters:
+            if converged(job.fits, tol, relative) or job.iters >= max_iters:
                 break
         job.result = {"factors": [f.cpu() for f in t.factors(dtype=torch.float32)], "lambda": t.lam()}
         job.finished_at = clock() - t0
@@ -281,4 +309,5 @@ def latency_stats(done: Sequence[JobState]) -> dict:
     last = max(j.finished_at for j in done)
     return {"jobs": len(lat), "p50_s": pct(50), "p99_s": pct(99), "mean_s": sum(lat) / len(lat),
             "jobs_per_s": len(lat) / max(last - first, 1e-9),
-            "mean_iters": sum(j.iters for j in done) / len(done)}
+            "mean_iters": sum(j.iters for j in done) / len(done),
+            "mean_final_fit": sum(j.fits[-1] for j in done if j.fits) / max(1, len(done))}

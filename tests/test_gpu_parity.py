@@ -387,3 +387,53 @@ def test_host_inputs_give_the_same_csr():
         a, b = t_host.csr(mode), t_dev.csr(mode)
         for key in ("fiber_ptr", "fiber_idx", "nz_ptr", "nz_idx", "nz_val"):
             assert torch.equal(a[key], b[key])
+
+
+@pytest.mark.parametrize("case", ["uniform10k", "zipf1M"])
+def test_bf16_als_fit_within_1e4_of_fp64_run(case):
+    """BF16 factor storage (FP32 accumulation, FP64 R x R solve and fit): five
+    ALS sweeps from the same start as the FP64 oracle's five sweeps; after
+    every sweep the fits differ by at most 1e-4 (the BF16 target)."""
+    if case == "uniform10k":
+        dims, R = [200, 150, 100], 10
+        idx, val = synth.uniform_tensor(dims, 10000, seed=14064520, device="cuda")
+    else:
+        dims, R = [20000, 10000, 5000], 16
+        idx, val = synth.zipf_tensor(dims, 1_000_000, [1.2, 1.2, 1.2], seed=61, device="cuda",
+                                     values="cp", R_true=R)
+    F = synth.normal_factors(dims, R, seed=62, device="cuda")
+    t = dfacto.Tensor(idx, val, dims, rank=R, factor_dtype=dfacto.BF16)
+    t.set_factors(F)
+    ot = as_oracle(idx, val, dims)
+    Fo = [host(f) for f in F]
+    for it in range(5):
+        st, fit = t.als_iter()
+        assert st == dfacto.OK
+        st_o, Fo, lam_o, fit_o = oracle.als_sweep(ot, Fo)
+        assert abs(fit - fit_o) <= 1e-4, (case, it, fit, fit_o)
+
+
+def test_gd_step_with_large_gradients():
+    """Factors scaled by 64 make the gradients ~1e13-1e14, so <X, [[GA, GB, GC]]>
+    (three gradient factors per nonzero) exceeds the FP32 range unless the
+    gradients are rescaled: the step still matches the oracle (alpha identical,
+    objective within ray_tolerance, factors 1e-5) and everything stays finite."""
+    dims = [100, 80, 60]
+    R = 8
+    idx, val = synth.uniform_tensor(dims, 5000, seed=711, device="cuda")
+    F = [64.0 * f for f in synth.normal_factors(dims, R, seed=712, device="cuda")]
+    t = dfacto.Tensor(idx, val, dims, rank=R)
+    t.set_factors(F)
+    ot = as_oracle(idx, val, dims)
+    before = [host(f) for f in t.factors()]
+    G = oracle.gd_gradient(ot, before)
+    assert max(np.abs(g).max() for g in G) > 1e13
+    st, loss, alpha = t.gd_iter()
+    st_o, Fo, alpha_o, loss_o, g2 = oracle.gd_step(ot, before, 0.0)
+    assert st == dfacto.OK and st_o == oracle.OK
+    assert np.isfinite(loss) and alpha == alpha_o, (loss, alpha, alpha_o)
+    tol = ray_tolerance(ot, before, G, alpha_o, 0.0)
+    assert abs(loss - loss_o) <= tol, (loss, loss_o, tol)
+    after = [host(f) for f in t.factors()]
+    for m in range(3):
+        assert rel(after[m], Fo[m]) <= 1e-5

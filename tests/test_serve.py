@@ -66,9 +66,9 @@ def specs(n, arrivals, nnz=1000, dims=(100, 100, 100), rank=8):
 
 
 def converge_sweep(rate, tol):
-    """First k >= 2 with |(1 - rate^k) - (1 - rate^(k-1))| < tol."""
+    """First k >= 2 with |fit_k - fit_{k-1}| < tol |fit_{k-1}|, fit_k = 1 - rate^k."""
     k = 2
-    while abs(rate ** k - rate ** (k - 1)) >= tol:
+    while abs(rate ** k - rate ** (k - 1)) >= tol * abs(1 - rate ** (k - 1)):
         k += 1
     return k
 
@@ -120,6 +120,35 @@ def test_rebuilds_are_throttled():
     assert len(done) == n
     sim_time = max(j.finished_at for j in done)
     assert eng.rebuilds <= sim_time / 0.02 + 3
+
+
+def test_retirements_alone_rebuild_only_past_the_waste_limit():
+    """A burst of 40 equal jobs finishing at 40 different sweeps: without
+    admissions, the batch is rebuilt only when finished jobs hold half of its
+    nonzeros, so the rebuilds halve the batch each time (about log2(40) + 1 of
+    them), not one per retirement."""
+    import math
+    n = 40
+    rates = {i: 0.05 + 0.02 * i for i in range(n)}
+    done, eng = run(specs(n, [0.0] * n), rates, max_iters=1000, tol=1e-4, relative=False)
+    assert len(done) == n
+    assert eng.rebuilds <= math.log2(n) + 2, eng.rebuilds
+
+
+def test_absolute_criterion():
+    rates = {0: 0.5}
+    done, eng = run(specs(1, [0.0]), rates, max_iters=50, tol=1e-3, relative=False)
+    k = 2
+    while abs(0.5 ** k - 0.5 ** (k - 1)) >= 1e-3:
+        k += 1
+    assert done[0].iters == k
+
+
+def test_converged_rule():
+    assert not serve.converged([0.5], 1e-4)
+    assert serve.converged([0.5, 0.50001], 1e-4)          # relative change 2e-5
+    assert not serve.converged([0.001, 0.0011], 1e-4)     # relative change 0.1
+    assert serve.converged([0.001, 0.0011], 1e-3, relative=False)
 
 
 def test_cap_applies_when_fit_keeps_moving():
