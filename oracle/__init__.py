@@ -26,16 +26,26 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 OK, EINVAL, ERANGE, EDUP, ENOMEM, ESINGULAR, ELSFAIL = 0, 1, 2, 3, 4, 6, 7
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into oracle/liboracle.so (if stale)."""
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + ".%d.tmp" % os.getpid()
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc into oracle/liboracle.so (if stale).  With
+    openmp=True, the same source with -fopenmp into oracle/liboracle_omp.so:
+    the multi-core CPU timing baseline (its pragmas parallelise the per-nonzero
+    sums with per-thread partial sums, so only the summation order differs;
+    the tests use the single-threaded build)."""
+    lib = _LIB_OMP if openmp else _LIB
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= os.path.getmtime(_SRC)):
+        return lib
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    if openmp:
+        cmd.insert(1, "-fopenmp")
     subprocess.check_call(cmd)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 _lib = None

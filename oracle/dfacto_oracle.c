@@ -158,7 +158,11 @@ void orc_mttkrp(int mode, int64_t nnz, const int32_t* idx, const float* val,
                 const double* C, double* out) {
   const double* F[3] = {A, B, C};
   const int o = ax_o(mode), in = ax_in(mode), f = ax_f(mode);
-  memset(out, 0, sizeof(double) * (size_t)dims[o] * (size_t)R);
+  const int64_t len = (int64_t)dims[o] * R;
+  memset(out, 0, sizeof(double) * (size_t)len);
+  /* (The pragma only matters for the multi-core timing build: each thread
+     sums into a private copy of out, added at the end.) */
+#pragma omp parallel for reduction(+ : out[0:len])
   for (int64_t t = 0; t < nnz; ++t) {
     const int64_t io = idx[(int64_t)o * nnz + t];
     const int64_t ii = idx[(int64_t)in * nnz + t];
@@ -208,7 +212,9 @@ int orc_mttkrp_rows(int mode, int64_t nnz, const int32_t* idx, const float* val,
 
 /* G = F^T F for an n x R row-major F (the Grams in Eq. kr-product). */
 void orc_gram(int64_t n, int R, const double* F, double* G) {
-  memset(G, 0, sizeof(double) * (size_t)R * (size_t)R);
+  const int64_t RR = (int64_t)R * R;
+  memset(G, 0, sizeof(double) * (size_t)RR);
+#pragma omp parallel for reduction(+ : G[0:RR])
   for (int64_t i = 0; i < n; ++i)
     for (int r = 0; r < R; ++r)
       for (int s = 0; s < R; ++s) G[r * R + s] += F[i * R + r] * F[i * R + s];
@@ -323,10 +329,10 @@ int orc_solve_normal(int64_t n, int R, const double* Gamma, const double* Nmat, 
   if (!L) return ORC_ENOMEM;
   memcpy(L, Gamma, sizeof(double) * (size_t)R * R);
   if (chol_lower(R, L) == 0) {
-    double* y = (double*)malloc(sizeof(double) * (size_t)R);
-    if (!y) { free(L); return ORC_ENOMEM; }
+#pragma omp parallel for
     for (int64_t i = 0; i < n; ++i) {
       /* x Gamma = b  <=>  Gamma x^T = b^T  <=>  L L^T x^T = b^T */
+      double y[R];
       for (int r = 0; r < R; ++r) {
         double s = Nmat[i * R + r];
         for (int k = 0; k < r; ++k) s -= L[r * R + k] * y[k];
@@ -338,7 +344,6 @@ int orc_solve_normal(int64_t n, int R, const double* Gamma, const double* Nmat, 
         X[i * R + r] = s / L[r * R + r];
       }
     }
-    free(y);
     free(L);
     return ORC_OK;
   }
@@ -347,6 +352,7 @@ int orc_solve_normal(int64_t n, int R, const double* Gamma, const double* Nmat, 
   if (!P) return ORC_ENOMEM;
   int st = orc_pinv_sym(R, Gamma, P);
   if (st != ORC_OK) { free(P); return st; }
+#pragma omp parallel for
   for (int64_t i = 0; i < n; ++i)
     for (int r = 0; r < R; ++r) {
       double s = 0.0;
@@ -391,6 +397,7 @@ int orc_als_mode_update(int mode, int64_t nnz, const int32_t* idx, const float* 
     for (int s = 0; s < R; ++s) Gf[r * R + s] *= Gi[r * R + s];
   for (int r = 0; r < R; ++r) Gf[r * R + r] += lambda_reg;
   int st = orc_solve_normal(n, R, Gf, Nm, F[o]);
+#pragma omp parallel for
   for (int r = 0; r < R; ++r) {
     double s = 0.0;
     for (int64_t i = 0; i < n; ++i) s += F[o][i * R + r] * F[o][i * R + r];
@@ -417,6 +424,7 @@ double orc_norm2(int64_t nnz, const float* val) {
 double orc_inner(int64_t nnz, const int32_t* idx, const float* val, int R,
                  const double* lambda, const double* A, const double* B, const double* C) {
   double s = 0.0;
+#pragma omp parallel for reduction(+ : s)
   for (int64_t t = 0; t < nnz; ++t) {
     const int64_t i = idx[t], j = idx[nnz + t], k = idx[2 * nnz + t];
     double m = 0.0;
