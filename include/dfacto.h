@@ -223,7 +223,7 @@ dfacto_status dfacto_als_iter(dfacto_t* h, double* fit_out);
  * Eq. gd-A): the three gradients dF_n = -N_n + F_n Gamma_n (+ lambda_reg F_n) at
  * the current point, then a backtracking line search -- alpha0 = min(2
  * alpha_prev, 1) (1 on the first step), accept the first alpha with
- * f(theta - alpha grad) <= f(theta) - 1e-4 alpha ||grad||^2, halving at most 40
+ * f(theta - alpha grad) <= f(theta) - 1e-4 alpha ||grad||^2, halving at most 100
  * times -- and the update theta <- theta - alpha grad.  f is the objective of
  * Eq. gd-obj-fn (regularized: Eq. gd-obj-fn-reg), evaluated in FP64.
  *   loss_out, alpha_out  host doubles, nullable; when both are NULL the call

@@ -565,7 +565,7 @@ int orc_gd_gradient(int64_t nnz, const int32_t* idx, const float* val, const int
  *   2. step size by backtracking (the paper only says a backtracking line search
  *      was used): alpha0 = min(2 * alpha_prev, 1) (1 if alpha_prev <= 0); accept
  *      the first alpha with f(theta - alpha grad) <= f(theta) - 1e-4 alpha g2,
- *      halving up to 40 trials; each trial evaluates f from scratch;
+ *      halving up to 100 trials; each trial evaluates f from scratch;
  *   3. A <- A - alpha dA, B <- B - alpha dB, C <- C - alpha dC.
  * On failure the factors are left unchanged and ORC_ELSFAIL is returned.
  * *alpha_io carries alpha_prev in and the accepted alpha out; *loss_out gets the
@@ -589,7 +589,7 @@ int orc_gd_step(int64_t nnz, const int32_t* idx, const float* val, const int32_t
   double alpha = (*alpha_io > 0.0) ? fmin(2.0 * (*alpha_io), 1.0) : 1.0;
   int accepted = 0;
   double fa = f0;
-  for (int trial = 0; trial < 40; ++trial) {
+  for (int trial = 0; trial < 100; ++trial) {
     for (int m = 0; m < 3; ++m)
       for (int64_t t = 0; t < (int64_t)dims[m] * R; ++t) T[m][t] = F[m][t] - alpha * G[m][t];
     fa = orc_loss(nnz, idx, val, dims, R, lambda_reg, T[0], T[1], T[2]);

@@ -32,6 +32,11 @@ constexpr int kT = 256;          // threads of the row-pass and Gram kernels
 constexpr int kTile = 64;        // rows per staged tile
 constexpr int kFoldTiles = 8;    // tiles summed in FP32 before folding into FP64
 constexpr int kMaxBlocks = 152 * 4;
+// Armijo trials of the GD line search (halvings of the step).  Each trial is an
+// evaluation of the exact polynomial, so trials cost nothing; 100 halvings
+// reach steps of 2^-100, far below the ~1e-14 that N(0,1) starting factors need
+// on 1e6-row tensors (Gamma's diagonal ~ the product of two dimensions).
+constexpr int kLineSearchTrials = 100;
 
 unsigned row_blocks(int64_t rows) {
   const int64_t b = (rows + 4 * kTile - 1) / (4 * kTile);
@@ -813,7 +818,7 @@ __global__ void __launch_bounds__(256) gd_line_search(const double* __restrict__
   double alpha = prev > 0.0 ? fmin(2.0 * prev, 1.0) : 1.0;
   bool ok = false;
   double fa = f0;
-  for (int trial = 0; trial < 40; ++trial) {
+  for (int trial = 0; trial < kLineSearchTrials; ++trial) {
     fa = f(alpha);
     if (fa <= f0 - 1e-4 * alpha * g2) {
       ok = true;
@@ -855,11 +860,14 @@ __global__ void gd_update(T* __restrict__ F, const float* __restrict__ grad, int
 // write and a read of N Gamma^{-1} in between.  Gamma^{-1} sits in shared
 // memory as RT x RT (zero-padded), read by broadcast.
 // ---------------------------------------------------------------------------
-constexpr int kPassRowsPerBlock = 1024;
+// Blocks of a row pass: one per 256-row tile up to one full wave (two
+// resident blocks per SM at 128 registers), so that large passes run as one
+// balanced wave of equal chunks.
+constexpr int kPassWave = 152 * 2;
 
 int pass_blocks(int64_t rows) {
-  const int64_t b = (rows + kPassRowsPerBlock - 1) / kPassRowsPerBlock;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(b, kMaxBlocks));
+  const int64_t tiles = (rows + kT - 1) / kT;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, kPassWave));
 }
 
 // Row r of N (R columns) zero-padded to RT.
@@ -1243,7 +1251,14 @@ __global__ void __launch_bounds__(kT) fit_from_parts_batch(const DenseJob* __res
 
 }  // namespace
 
-int dense_row_blocks(int64_t rows, int R) { return R <= 32 ? pass_blocks(rows) : (int)row_blocks(rows); }
+// Blocks of one job's row passes inside a batch: at least 1024 rows per block
+// (many jobs fill the GPU together; a block's fixed costs, the staging of
+// Gamma^{-1} and its R x R partial sums, are then paid per 1024 rows).
+int dense_row_blocks(int64_t rows, int R) {
+  if (R > 32) return (int)row_blocks(rows);
+  const int64_t b = (rows + 1023) / 1024;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, kMaxBlocks));
+}
 
 // ---------------------------------------------------------------------------
 // Host orchestration.

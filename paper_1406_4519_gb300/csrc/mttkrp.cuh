@@ -389,13 +389,22 @@ __global__ void __launch_bounds__(kWalkWarps * 32) mttkrp_walk(const MttkrpParam
 // The merge of rows shared between segments, warps and CTAs is the one of
 // mttkrp_walk.
 // ---------------------------------------------------------------------------
-// VEC consecutive floats in shared memory, one vector access where VEC allows.
-template <int VEC>
+// A thread's VEC parked floats in shared memory.  Slot k of thread tid holds
+// them as VEC/4 float4 chunks, chunk q at ((k * VEC/4 + q) * NT + tid) * 4, so
+// that a warp's accesses to one chunk are consecutive 16-byte words (no bank
+// conflicts); VEC < 4 keeps the VEC floats together at (k * NT + tid) * VEC.
+template <int VEC, int NT>
+__device__ __forceinline__ float* park_slot(float* vb, int k, int tid) {
+  if constexpr (VEC % 4 == 0) return vb + ((size_t)k * (VEC / 4) * NT + tid) * 4;
+  else return vb + ((size_t)k * NT + tid) * VEC;
+}
+template <int VEC, int NT>
 __device__ __forceinline__ void smem_st(float* p, const float (&v)[VEC]) {
   if constexpr (VEC % 4 == 0) {
 #pragma unroll
     for (int e = 0; e < VEC; e += 4)
-      *reinterpret_cast<float4*>(p + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+      *reinterpret_cast<float4*>(p + (size_t)(e / 4) * NT * 4) =
+          make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
   } else if constexpr (VEC == 2) {
     *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
   } else {
@@ -403,12 +412,12 @@ __device__ __forceinline__ void smem_st(float* p, const float (&v)[VEC]) {
     for (int e = 0; e < VEC; ++e) p[e] = v[e];
   }
 }
-template <int VEC>
+template <int VEC, int NT>
 __device__ __forceinline__ void smem_ld(const float* p, float (&v)[VEC]) {
   if constexpr (VEC % 4 == 0) {
 #pragma unroll
     for (int e = 0; e < VEC; e += 4) {
-      const float4 t = *reinterpret_cast<const float4*>(p + e);
+      const float4 t = *reinterpret_cast<const float4*>(p + (size_t)(e / 4) * NT * 4);
       v[e] = t.x; v[e + 1] = t.y; v[e + 2] = t.z; v[e + 3] = t.w;
     }
   } else if constexpr (VEC == 2) {
@@ -451,7 +460,7 @@ __device__ __forceinline__ void walk2_cta(const MttkrpParams& a, int cta, float*
   const int R = a.R;
   float* s_val = smem;                           // [SEGS * 2][R]
   float* w_val = smem + (size_t)SEGS * 2 * R;    // [kWalkWarps * 2][R]
-  float* vb = w_val + (size_t)kWalkWarps * 2 * R;  // [U][NT][VEC] parked fiber sums
+  float* vb = w_val + (size_t)kWalkWarps * 2 * R;  // U slots of NT x VEC parked fiber sums
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -535,7 +544,7 @@ __device__ __forceinline__ void walk2_cta(const MttkrpParams& a, int cta, float*
         for (int e = 0; e < VEC; ++e) v[e] = fmaf(x, fin[uu][e], v[e]);
         const bool end = p < p1 && ((ebits >> (u0 + uu)) & 1u);
         if (end) {
-          smem_st<VEC>(vb + ((size_t)k * NT + tid) * VEC, v);
+          smem_st<VEC, NT>(park_slot<VEC, NT>(vb, k, tid), v);
 #pragma unroll
           for (int e = 0; e < VEC; ++e) v[e] = 0.f;
         }
@@ -569,7 +578,7 @@ __device__ __forceinline__ void walk2_cta(const MttkrpParams& a, int cta, float*
         for (int j = 0; j < CC; ++j) {
           if (j0 + j < k) {
             float vv[VEC];
-            smem_ld<VEC>(vb + ((size_t)(j0 + j) * NT + tid) * VEC, vv);
+            smem_ld<VEC, NT>(park_slot<VEC, NT>(vb, j0 + j, tid), vv);
             fold(rj[j], vv, ff[j]);
           }
         }

@@ -410,7 +410,7 @@ def test_gd_step_armijo_backtracking(seed, scale):
 
     def backtrack(a, F, G, f0, g2):
         n = 0
-        for _ in range(40):
+        for _ in range(100):
             if dense_loss(X, [f - a * g for f, g in zip(F, G)], 0.0) <= f0 - 1e-4 * a * g2:
                 break
             a *= 0.5
