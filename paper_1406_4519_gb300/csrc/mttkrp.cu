@@ -113,10 +113,10 @@ WalkCfg choose_walk(int R, int dtype, int64_t nnz, int64_t nfib, int seg_opt, in
   (void)nnz;
   (void)nfib;
   WalkCfg c;
-  // Default: eight columns per lane (one 16-byte BF16 load, two FP32 loads)
-  // from R = 32 up, else one 16-byte load per lane (4 FP32 or 8 BF16 columns):
-  // measured fastest on the 50M-nonzero power-law workload at R = 16 and 32.
-  int vec = vec_opt > 0 ? vec_opt : ((dtype == DFACTO_BF16 || R >= 32) ? 8 : 4);
+  // Default: one 16-byte load per lane and factor row (4 FP32 or 8 BF16
+  // columns), measured fastest on the 50M-nonzero power-law workload at
+  // R = 16 and 32.
+  int vec = vec_opt > 0 ? vec_opt : (dtype == DFACTO_BF16 ? 8 : 4);
   while (vec > 1 && (R % vec) != 0) vec >>= 1;
   int G = next_pow2((R + vec - 1) / vec);
   while (G > 32 && vec < 8 && (R % (vec * 2)) == 0) {

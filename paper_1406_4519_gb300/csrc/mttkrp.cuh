@@ -437,12 +437,14 @@ template <typename T, int VEC, int G>
 struct Walk2Shape {
   static constexpr int NG = 32 / G;
   static constexpr int SEGS = kWalkWarps * NG;
-  static constexpr int U = (G < 32 / VEC) ? G : (32 / VEC);
+  // Gathers in flight per lane: at most 16 gathered values (U * VEC <= 16);
+  // more leave the kernel short of registers (spills) at the budget below.
+  static constexpr int U = (G < 16 / VEC) ? G : (16 / VEC);
   // Resident CTAs per SM the register budget is cut for: the kernel is bound by
-  // the latency of its gathers, so occupancy pays more than a few spilled
-  // registers.  With U * VEC <= 16 gathered values per lane it fits 64
-  // registers (4 CTAs), otherwise 80 (3 CTAs).
-  static constexpr int MIN_BLOCKS = (U * VEC <= 16) ? 4 : 3;
+  // the latency of its gathers and its L1 traffic, so occupancy pays more than
+  // a few registers: 80 registers (3 CTAs) for eight-column lanes, 64 (4 CTAs)
+  // for narrower ones.
+  static constexpr int MIN_BLOCKS = VEC >= 8 ? 3 : 4;
   static size_t smem_bytes(int R) {
     return sizeof(float) * ((size_t)(2 * SEGS + 2 * kWalkWarps) * R + (size_t)kWalkWarps * 32 * U * VEC);
   }
