@@ -20,6 +20,7 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "mttkrp.cuh"
 
 namespace dfacto {
 namespace {
@@ -31,6 +32,7 @@ struct DualParams {
   const int32_t* nz_idx;
   const float* nz_val;
   const int32_t* seg_fib;
+  const uint32_t* end_bits;  // dual_walk2: bit p set iff nonzero p ends its fiber
   const void* A;
   const void* B;
   const void* C;
@@ -162,6 +164,201 @@ __global__ void __launch_bounds__(kWalkWarps * 32) dual_walk(const DualParams a)
   }
 }
 
+// ---------------------------------------------------------------------------
+// dual_walk2: the same four terms with the organisation of mttkrp_walk2: fiber
+// ends from the end bitmask of the mode-1 copy, both fiber sums (vB, vG) parked
+// in shared memory where a fiber ends, and the closed fibers folded CC at a
+// time (their C and GC rows gathered together).  At most 8 values of each of
+// the two gathered rows (B and GB) are in flight per lane.
+// ---------------------------------------------------------------------------
+template <int VEC>
+struct Dual2Shape {
+  static constexpr int NT = kWalkWarps * 32;
+  static constexpr int U = 8 / VEC > 0 ? 8 / VEC : 1;  // capped by G below
+  static constexpr int CC = 2;                           // fibers folded per round
+};
+
+template <typename T, int VEC, int G>
+__global__ void __launch_bounds__(kWalkWarps * 32, 3) dual_walk2(const DualParams a) {
+  constexpr int NG = 32 / G;
+  constexpr int SEGS = kWalkWarps * NG;
+  constexpr int NT = Dual2Shape<VEC>::NT;
+  constexpr int U = G < Dual2Shape<VEC>::U ? G : Dual2Shape<VEC>::U;
+  constexpr int CC = Dual2Shape<VEC>::CC < U ? Dual2Shape<VEC>::CC : U;
+  extern __shared__ __align__(16) float vb[];  // 2U slots of NT x VEC parked sums
+  __shared__ double s_t[kWalkWarps][4];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int g = lane / G, c = lane % G;
+  const int gbase = g * G;
+  const int col0 = c * VEC;
+  const bool colok = col0 < a.R;
+  const int sl = warp * NG + g;
+  const int nnz = (int)a.nnz;
+  const int p0 = (int)min(((int64_t)blockIdx.x * SEGS + sl) * a.seg, a.nnz);
+  const int p1 = min(p0 + a.seg, nnz);
+  const bool active = p0 < nnz;
+  const int R = a.R;
+  const T* __restrict__ A = static_cast<const T*>(a.A);
+  const T* __restrict__ B = static_cast<const T*>(a.B);
+  const T* __restrict__ C = static_cast<const T*>(a.C);
+  const float sA = a.gscale[0], sB = a.gscale[1], sC = a.gscale[2];
+
+  float vB[VEC], vG[VEC], u1[VEC], u2[VEC], u3[VEC];
+#pragma unroll
+  for (int e = 0; e < VEC; ++e) vB[e] = vG[e] = u1[e] = u2[e] = u3[e] = 0.f;
+  float t[4] = {0.f, 0.f, 0.f, 0.f};
+  int q = 0, row_cur = -1;
+  if (active) {
+    q = a.seg_fib[(int64_t)blockIdx.x * SEGS + sl];
+    row_cur = a.fiber_row[q];
+  }
+  // Close row row_cur: T110 += GA.u1, T101 += GA.u2, T011 += A.u3, T111 += GA.u3.
+  auto emit_row = [&]() {
+    if (colok) {
+      float ar[VEC], gar[VEC];
+      VecIO<T, VEC>::load(A + (int64_t)row_cur * R + col0, ar);
+      VecIO<float, VEC>::load(a.GA + (int64_t)row_cur * R + col0, gar);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const float ga = gar[e] * sA;
+        t[0] = fmaf(ga, u1[e], t[0]);
+        t[1] = fmaf(ga, u2[e], t[1]);
+        t[2] = fmaf(ar[e], u3[e], t[2]);
+        t[3] = fmaf(ga, u3[e], t[3]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) u1[e] = u2[e] = u3[e] = 0.f;
+  };
+  // Fold a closed fiber (row r, sums pB / pG, rows cf = C[k], gcf = GC[k]).
+  auto fold = [&](int r, const float (&pB)[VEC], const float (&pG)[VEC], const float (&cf)[VEC],
+                  const float (&gcf)[VEC]) {
+    if (r != row_cur) {
+      emit_row();
+      row_cur = r;
+    }
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      u1[e] = fmaf(cf[e], pG[e], u1[e]);
+      u2[e] = fmaf(gcf[e], pB[e], u2[e]);
+      u3[e] = fmaf(gcf[e], pG[e], u3[e]);
+    }
+  };
+
+  for (int base = p0; base < p0 + a.seg; base += G) {
+    const int pl = base + c;
+    const bool okl = pl < p1;
+    const int my_in = okl ? __ldg(a.nz_idx + pl) : 0;
+    const float my_x = okl ? __ldg(a.nz_val + pl) : 0.f;
+    const uint32_t ebits =
+        (active && base < p1) ? (__ldg(a.end_bits + (base >> 5)) >> (base & 31)) : 0u;
+#pragma unroll
+    for (int u0 = 0; u0 < G; u0 += U) {
+      float b[U][VEC], gb[U][VEC];
+#pragma unroll
+      for (int uu = 0; uu < U; ++uu) {
+        const int j = __shfl_sync(kFull, my_in, gbase + u0 + uu);
+        if (colok && base + u0 + uu < p1) {
+          VecIO<T, VEC>::load(B + (int64_t)j * R + col0, b[uu]);
+          VecIO<float, VEC>::load(a.GB + (int64_t)j * R + col0, gb[uu]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) b[uu][e] = gb[uu][e] = 0.f;
+        }
+      }
+      int k = 0;
+#pragma unroll
+      for (int uu = 0; uu < U; ++uu) {
+        const float x = __shfl_sync(kFull, my_x, gbase + u0 + uu);
+        const int p = base + u0 + uu;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+          vB[e] = fmaf(x, b[uu][e], vB[e]);
+          vG[e] = fmaf(x, gb[uu][e] * sB, vG[e]);
+        }
+        const bool end = p < p1 && ((ebits >> (u0 + uu)) & 1u);
+        if (end) {
+          smem_st<VEC, NT>(park_slot<VEC, NT>(vb, 2 * k, tid), vB);
+          smem_st<VEC, NT>(park_slot<VEC, NT>(vb, 2 * k + 1, tid), vG);
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) vB[e] = vG[e] = 0.f;
+        }
+        k += end ? 1 : 0;
+      }
+      for (int j0 = 0; j0 < k; j0 += CC) {
+        int rj[CC];
+        float cf[CC][VEC], gcf[CC][VEC];
+#pragma unroll
+        for (int j = 0; j < CC; ++j) {
+          rj[j] = row_cur;
+          if (j0 + j < k) {
+            const int kk = __ldg(a.fiber_idx + q + j0 + j);
+            rj[j] = __ldg(a.fiber_row + q + j0 + j);
+            if (colok) {
+              VecIO<T, VEC>::load(C + (int64_t)kk * R + col0, cf[j]);
+              VecIO<float, VEC>::load(a.GC + (int64_t)kk * R + col0, gcf[j]);
+            }
+          }
+          if (!(j0 + j < k && colok)) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) cf[j][e] = gcf[j][e] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < CC; ++j) {
+          if (j0 + j < k) {
+            float pB[VEC], pG[VEC];
+            smem_ld<VEC, NT>(park_slot<VEC, NT>(vb, 2 * (j0 + j), tid), pB);
+            smem_ld<VEC, NT>(park_slot<VEC, NT>(vb, 2 * (j0 + j) + 1, tid), pG);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) gcf[j][e] *= sC;
+            fold(rj[j], pB, pG, cf[j], gcf[j]);
+          }
+        }
+      }
+      q += k;
+    }
+  }
+  if (active) {
+    // the fiber open at the segment end (its last nonzero lies beyond p1)
+    if (!((__ldg(a.end_bits + ((p1 - 1) >> 5)) >> ((p1 - 1) & 31)) & 1u)) {
+      const int kk = __ldg(a.fiber_idx + q);
+      const int r = __ldg(a.fiber_row + q);
+      float cf[VEC], gcf[VEC];
+      if (colok) {
+        VecIO<T, VEC>::load(C + (int64_t)kk * R + col0, cf);
+        VecIO<float, VEC>::load(a.GC + (int64_t)kk * R + col0, gcf);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) cf[e] = gcf[e] = 0.f;
+      }
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) gcf[e] *= sC;
+      fold(r, vB, vG, cf, gcf);
+    }
+    emit_row();
+  }
+  double td[4];
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    td[kk] = warp_sum((double)t[kk]);
+    if (lane == 0) s_t[warp][kk] = td[kk];
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double sum = 0.0;
+    for (int w = 0; w < kWalkWarps; ++w) sum += s_t[w][threadIdx.x];
+    a.part[(size_t)blockIdx.x * 4 + threadIdx.x] = sum;
+  }
+}
+
+template <int VEC, int G>
+size_t dual2_smem() {
+  constexpr int U = G < Dual2Shape<VEC>::U ? G : Dual2Shape<VEC>::U;
+  return sizeof(float) * (size_t)2 * U * Dual2Shape<VEC>::NT * VEC;
+}
+
 // scal[kT110 + k] = sum over CTAs of part[b][k], k = 0..3 (fixed order:
 // strided per-thread sums, then a fixed tree), divided by the term's scales.
 __global__ void __launch_bounds__(256) dual_reduce(const double* __restrict__ part, int64_t ncta,
@@ -213,15 +410,20 @@ __global__ void grad_scales(const unsigned* __restrict__ maxbits, float* __restr
 }
 
 template <typename T, int VEC, int G>
-cudaError_t go(const DualParams& a, int64_t ncta, cudaStream_t s) {
-  dual_walk<T, VEC, G><<<(unsigned)ncta, kWalkWarps * 32, 0, s>>>(a); DF_COUNT();
+cudaError_t go(const DualParams& a, int64_t ncta, cudaStream_t s, int kernel) {
+  if (kernel == 2) {
+    dual_walk2<T, VEC, G><<<(unsigned)ncta, kWalkWarps * 32, dual2_smem<VEC, G>(), s>>>(a);
+  } else {
+    dual_walk<T, VEC, G><<<(unsigned)ncta, kWalkWarps * 32, 0, s>>>(a);
+  }
+  DF_COUNT();
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch(int vec, int G, const DualParams& a, int64_t ncta, cudaStream_t s) {
+cudaError_t launch(int vec, int G, const DualParams& a, int64_t ncta, cudaStream_t s, int kernel) {
 #define DF_CASE(V, GG) \
-  if (vec == V && G == GG) return go<T, V, GG>(a, ncta, s);
+  if (vec == V && G == GG) return go<T, V, GG>(a, ncta, s, kernel);
   DF_CASE(1, 1) DF_CASE(1, 2) DF_CASE(1, 4) DF_CASE(1, 8) DF_CASE(1, 16) DF_CASE(1, 32)
   DF_CASE(2, 1) DF_CASE(2, 2) DF_CASE(2, 4) DF_CASE(2, 8) DF_CASE(2, 16) DF_CASE(2, 32)
   DF_CASE(4, 1) DF_CASE(4, 2) DF_CASE(4, 4) DF_CASE(4, 8) DF_CASE(4, 16) DF_CASE(4, 32)
@@ -236,7 +438,15 @@ dfacto_status dual_pass(dfacto_t* h) {
   ModeCSR& M = h->m[0];
   dfacto_status st = ensure_segments(h, 0);
   if (st != DFACTO_OK) return st;
-  const WalkCfg cfg = M.cfg;
+  // The mode-1 walk's segments; dual_walk2 keeps five accumulators and two
+  // gathered rows per lane, so its lanes take at most four columns.
+  WalkCfg cfg = M.cfg;
+  if (cfg.kernel == 2 && cfg.vec > 4) {
+    cfg.vec = 4;
+    int G = 1;
+    while (G * 4 < h->R) G <<= 1;
+    cfg.G = G;
+  }
   const int segs = kWalkWarps * (32 / cfg.G);
   const int64_t P = (int64_t)segs * cfg.seg;
   const int64_t ncta = (h->nnz + P - 1) / P;
@@ -262,6 +472,7 @@ dfacto_status dual_pass(dfacto_t* h) {
   a.nz_idx = M.nz_idx;
   a.nz_val = M.nz_val;
   a.seg_fib = M.seg_fib;
+  a.end_bits = M.end_bits;
   a.A = h->F[0];
   a.B = h->F[1];
   a.C = h->F[2];
@@ -275,8 +486,8 @@ dfacto_status dual_pass(dfacto_t* h) {
   a.R = h->R;
   a.seg = cfg.seg;
   cudaError_t e = (h->dtype == DFACTO_BF16)
-                      ? launch<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, h->stream)
-                      : launch<float>(cfg.vec, cfg.G, a, ncta, h->stream);
+                      ? launch<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, h->stream, cfg.kernel)
+                      : launch<float>(cfg.vec, cfg.G, a, ncta, h->stream, cfg.kernel);
   if (e != cudaSuccess) return cuda_fail(h, e, "dual_walk launch");
   dual_reduce<<<1, 256, 0, h->stream>>>(h->partials, ncta, gscale, h->scal); DF_COUNT();
   DF_CUDA(h, cudaGetLastError());
