@@ -31,6 +31,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_EINVAL 1
@@ -160,9 +163,33 @@ void orc_mttkrp(int mode, int64_t nnz, const int32_t* idx, const float* val,
   const int o = ax_o(mode), in = ax_in(mode), f = ax_f(mode);
   const int64_t len = (int64_t)dims[o] * R;
   memset(out, 0, sizeof(double) * (size_t)len);
-  /* (The pragma only matters for the multi-core timing build: each thread
-     sums into a private copy of out, added at the end.) */
-#pragma omp parallel for reduction(+ : out[0:len])
+#ifdef _OPENMP
+  /* Multi-core timing build only: each thread sums its share of the nonzeros
+     into its own heap copy of out; the copies are added at the end. */
+  {
+    const int nth = omp_get_max_threads();
+    double* priv = nth > 1 ? (double*)calloc((size_t)nth * (size_t)len, sizeof(double)) : NULL;
+    if (priv) {
+#pragma omp parallel
+      {
+        double* my = priv + (size_t)omp_get_thread_num() * (size_t)len;
+#pragma omp for
+        for (int64_t t = 0; t < nnz; ++t) {
+          const int64_t io = idx[(int64_t)o * nnz + t];
+          const int64_t ii = idx[(int64_t)in * nnz + t];
+          const int64_t iff = idx[(int64_t)f * nnz + t];
+          const double x = (double)val[t];
+          for (int r = 0; r < R; ++r) my[io * R + r] += x * F[in][ii * R + r] * F[f][iff * R + r];
+        }
+      }
+#pragma omp parallel for
+      for (int64_t e = 0; e < len; ++e)
+        for (int th = 0; th < nth; ++th) out[e] += priv[(size_t)th * (size_t)len + e];
+      free(priv);
+      return;
+    }
+  }
+#endif
   for (int64_t t = 0; t < nnz; ++t) {
     const int64_t io = idx[(int64_t)o * nnz + t];
     const int64_t ii = idx[(int64_t)in * nnz + t];
