@@ -19,8 +19,9 @@ pytestmark = pytest.mark.gpu
 MTTKRP_TOL = 1e-5
 
 # Jobs of mixed rank, factor type, size and skew: ranks 8/16/32 share three
-# rank classes of the batched kernel, R = 10 takes its own walk launch, two
-# jobs are BF16, one has an empty mode-0 majority and one has a single nonzero.
+# rank classes of the batched kernel, R = 10 and R = 40 take their own walk
+# launch, R = 40 and 64 the row passes for R > 32, three jobs are BF16, one has
+# an empty mode-0 majority and one has a single nonzero.
 JOB_SPECS = [
     dict(dims=[300, 200, 100], nnz=20000, R=8, seed=101),
     dict(dims=[1200, 90, 400], nnz=30000, R=16, seed=102, zipf=[1.2, 1.1, 1.3]),
@@ -31,6 +32,9 @@ JOB_SPECS = [
     dict(dims=[250, 250, 250], nnz=15000, R=8, seed=107, dtype=dfacto.BF16, zipf=[1.1, 1.1, 1.1]),
     dict(dims=[20, 30, 10], nnz=1, R=8, seed=108, twin_only=True),
     dict(dims=[900, 400, 300], nnz=45000, R=32, seed=109),
+    # R > 32: the row passes of the tiled kernels through the N Gamma^-1 buffer
+    dict(dims=[600, 300, 200], nnz=30000, R=40, seed=110),
+    dict(dims=[400, 350, 300], nnz=25000, R=64, seed=111, dtype=dfacto.BF16),
 ]
 
 

@@ -437,3 +437,24 @@ def test_gd_step_with_large_gradients():
     after = [host(f) for f in t.factors()]
     for m in range(3):
         assert rel(after[m], Fo[m]) <= 1e-5
+
+
+def test_gd_stepwise_bf16_factors():
+    """GD with BF16 factor storage, step-wise from the GPU's (BF16) state: the
+    accepted alpha is the oracle's and the new factors (rounded to BF16 on the
+    GPU) are within the BF16 bar, 1e-2 normwise, of the oracle's FP64 step."""
+    dims = [120, 90, 60]
+    R = 8
+    t, idx, val, F = make(dims, 8000, R, seed=730, dtype=dfacto.BF16)
+    ot = as_oracle(idx, val, dims)
+    alpha_prev = 0.0
+    for it in range(3):
+        before = [host(f) for f in t.factors()]
+        st, loss, alpha = t.gd_iter()
+        st_o, Fo, alpha_o, loss_o, g2 = oracle.gd_step(ot, before, alpha_prev)
+        assert st == dfacto.OK and st_o == oracle.OK
+        assert alpha == alpha_o, (it, alpha, alpha_o)
+        after = [host(f) for f in t.factors()]
+        for m in range(3):
+            assert rel(after[m], Fo[m]) <= 1e-2, (it, m)
+        alpha_prev = alpha
