@@ -1154,6 +1154,202 @@ __device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ 
   }
 }
 
+// Tile rows of a factor in storage type T (BF16 widened), coalesced 16-byte
+// loads where the layout allows.
+template <int LD>
+__device__ __forceinline__ void tile_load_T(const float* __restrict__ M, int64_t t0, int nt, int R,
+                                            float* __restrict__ tile) {
+  tile_load<LD>(M, t0, nt, R, tile);
+}
+template <int LD>
+__device__ __forceinline__ void tile_load_T(const __nv_bfloat16* __restrict__ M, int64_t t0, int nt,
+                                            int R, float* __restrict__ tile) {
+  const __nv_bfloat16* src = M + t0 * R;
+  const int total = nt * R;
+  if ((R & 7) == 0) {
+    for (int e8 = threadIdx.x; e8 < (total >> 3); e8 += kT) {
+      const uint4 w = __ldg(reinterpret_cast<const uint4*>(src) + e8);
+      const int e = 8 * e8, r = e / R, c = e - r * R;
+      float* q = tile + r * LD + c;
+      q[0] = bf16_lo(w.x); q[1] = bf16_hi(w.x); q[2] = bf16_lo(w.y); q[3] = bf16_hi(w.y);
+      q[4] = bf16_lo(w.z); q[5] = bf16_hi(w.z); q[6] = bf16_lo(w.w); q[7] = bf16_hi(w.w);
+    }
+  } else {
+    for (int e = threadIdx.x; e < total; e += kT) {
+      const int r = e / R, c = e - r * R;
+      tile[r * LD + c] = ld_elem(src + e);
+    }
+  }
+}
+
+// Sum the per-thread 4 x 4 block partials a32 of the groups of each block in
+// group order (FP64, four entries at a time through `scratch`, >= kT * 4
+// doubles) and store block vb's R x R partial at gpart[vb][R*R].
+template <int RT>
+__device__ __forceinline__ void store_gram_partial(const float (&a32)[16], double* scratch, int R,
+                                                   double* __restrict__ gpart, int vb) {
+  using PS = PassShape<RT>;
+  constexpr int NB4 = PS::NB4, NBLK = PS::NBLK, NGRP = PS::NGRP;
+  const int blk = threadIdx.x % NBLK, grp = threadIdx.x / NBLK;
+  const int bi = blk / NB4, bj = blk % NB4;
+  for (int q0 = 0; q0 < 16; q0 += 4) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) scratch[threadIdx.x * 4 + q] = (double)a32[q0 + q];
+    __syncthreads();
+    if (grp == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double t = 0.0;
+        for (int gg = 0; gg < NGRP; ++gg) t += scratch[(gg * NBLK + blk) * 4 + q];
+        const int e = q0 + q;
+        const int a = 4 * bi + e / 4, c = 4 * bj + e % 4;
+        if (a < R && c < R) gpart[(size_t)vb * R * R + a * R + c] = t;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// GD, one pass per mode for R <= 32: grad = -N + F Gamma (Gamma already holds
+// + lambda_reg I) stored, with the partials of the line search's matrices
+// P2 = grad^T grad (gg) and F^T grad (fg, symmetrised later into P1) and the
+// scalars spart[vb][3] = ||grad||^2, sum grad * N, sum F * N.  Tiles of kT rows
+// of N and F are staged with coalesced loads; thread t forms row t of grad
+// (F row t times Gamma, same arithmetic order as the other row passes) into
+// the N tile, which is then stored with coalesced stores.  Dynamic shared
+// memory: Gamma (RT x RT) and two tiles.
+template <typename T, int RT>
+__global__ void __launch_bounds__(kT, 2) gd_rows(const float* __restrict__ N, const T* __restrict__ F,
+                                                 const float* __restrict__ Gam32, int64_t rows, int R,
+                                                 float* __restrict__ grad,
+                                                 double* __restrict__ gpart_gg,
+                                                 double* __restrict__ gpart_fg,
+                                                 double* __restrict__ spart) {
+  using PS = PassShape<RT>;
+  constexpr int CW = PS::CW, LD = PS::LD, NB4 = PS::NB4, NBLK = PS::NBLK, NGRP = PS::NGRP;
+  extern __shared__ __align__(16) float dyn[];
+  float* Ws = dyn;                    // [RT * RT]
+  float* tN = Ws + RT * RT;           // [kT * LD] N, then grad
+  float* tF = tN + kT * LD;           // [kT * LD] F
+  __shared__ double red[kT];
+  stage_w<RT>(Gam32, R, Ws);
+  for (int e = threadIdx.x; e < 2 * kT * LD; e += kT) tN[e] = 0.f;
+  const int blk = threadIdx.x % NBLK, grp = threadIdx.x / NBLK;
+  const int bi = blk / NB4, bj = blk % NB4;
+  float agg[16], afg[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) agg[q] = afg[q] = 0.f;
+  double ad[3] = {0.0, 0.0, 0.0};
+  int64_t r0, r1;
+  block_rows(rows, blockIdx.x, gridDim.x, r0, r1);
+  for (int64_t t0 = r0; t0 < r1; t0 += kT) {
+    const int nt = (int)min((int64_t)kT, r1 - t0);
+    __syncthreads();
+    tile_load<LD>(N, t0, nt, R, tN);
+    tile_load_T<LD>(F, t0, nt, R, tF);
+    __syncthreads();
+    float af[3] = {0.f, 0.f, 0.f};
+    if ((int)threadIdx.x < nt) {
+      float* nrow = tN + threadIdx.x * LD;
+      float f[RT];
+#pragma unroll
+      for (int c4 = 0; c4 < RT / 4; ++c4) {
+        const float4 v = *reinterpret_cast<const float4*>(tF + threadIdx.x * LD + 4 * c4);
+        f[4 * c4] = v.x; f[4 * c4 + 1] = v.y; f[4 * c4 + 2] = v.z; f[4 * c4 + 3] = v.w;
+      }
+#pragma unroll
+      for (int h = 0; h < RT / CW; ++h) {
+        float o[CW];
+        row_solve<RT, CW>(f, Ws, h * CW, o);
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          const int col = h * CW + c;
+          const float nv = nrow[col];
+          const float gv = o[c] - nv;  // 0 in the padding columns
+          af[0] = fmaf(gv, gv, af[0]);
+          af[1] = fmaf(gv, nv, af[1]);
+          af[2] = fmaf(f[col], nv, af[2]);
+          nrow[col] = gv;
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) ad[t] += (double)af[t];
+    __syncthreads();
+    tile_store<LD>(tN, t0, nt, R, grad);
+    for (int i = grp; i < nt; i += NGRP) {
+      const float4 gx = *reinterpret_cast<const float4*>(tN + i * LD + 4 * bi);
+      const float4 gy = *reinterpret_cast<const float4*>(tN + i * LD + 4 * bj);
+      const float4 fx = *reinterpret_cast<const float4*>(tF + i * LD + 4 * bi);
+      const float ga[4] = {gx.x, gx.y, gx.z, gx.w}, gb[4] = {gy.x, gy.y, gy.z, gy.w};
+      const float fa[4] = {fx.x, fx.y, fx.z, fx.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          agg[u * 4 + w] = fmaf(ga[u], gb[w], agg[u * 4 + w]);
+          afg[u * 4 + w] = fmaf(fa[u], gb[w], afg[u * 4 + w]);
+        }
+    }
+  }
+  for (int t = 0; t < 3; ++t) {
+    const double v = block_sum(ad[t], red);
+    if (threadIdx.x == 0) spart[(size_t)blockIdx.x * 3 + t] = v;
+  }
+  __syncthreads();
+  double* scratch = reinterpret_cast<double*>(tN);
+  store_gram_partial<RT>(agg, scratch, R, gpart_gg, blockIdx.x);
+  store_gram_partial<RT>(afg, scratch, R, gpart_fg, blockIdx.x);
+}
+
+// GD update for R <= 32: F <- F - step * grad (step = scal[kStep], 0 after a
+// failed search), stored in T, with the Gram partials of the stored factor
+// (the Gram the next step needs).  Same staging as gd_rows.
+template <typename T, int RT>
+__global__ void __launch_bounds__(kT, 2) gd_update_gram(T* __restrict__ F, const float* __restrict__ grad,
+                                                        const double* __restrict__ scal, int64_t rows,
+                                                        int R, double* __restrict__ gpart) {
+  using PS = PassShape<RT>;
+  constexpr int LD = PS::LD, NB4 = PS::NB4, NBLK = PS::NBLK, NGRP = PS::NGRP;
+  extern __shared__ __align__(16) float dyn[];
+  float* tF = dyn;             // [kT * LD]
+  float* tG = tF + kT * LD;    // [kT * LD]
+  const float step = (float)scal[kStep];
+  for (int e = threadIdx.x; e < 2 * kT * LD; e += kT) tF[e] = 0.f;
+  const int blk = threadIdx.x % NBLK, grp = threadIdx.x / NBLK;
+  const int bi = blk / NB4, bj = blk % NB4;
+  float a32[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) a32[q] = 0.f;
+  int64_t r0, r1;
+  block_rows(rows, blockIdx.x, gridDim.x, r0, r1);
+  for (int64_t t0 = r0; t0 < r1; t0 += kT) {
+    const int nt = (int)min((int64_t)kT, r1 - t0);
+    __syncthreads();
+    tile_load_T<LD>(F, t0, nt, R, tF);
+    tile_load<LD>(grad, t0, nt, R, tG);
+    __syncthreads();
+    if ((int)threadIdx.x < nt) {
+      float* frow = tF + threadIdx.x * LD;
+      const float* grow = tG + threadIdx.x * LD;
+      for (int c = 0; c < R; ++c) frow[c] = rt_elem(F, frow[c] - step * grow[c]);
+    }
+    __syncthreads();
+    tile_store<LD>(tF, t0, nt, R, F);
+    for (int i = grp; i < nt; i += NGRP) {
+      const float4 xv = *reinterpret_cast<const float4*>(tF + i * LD + 4 * bi);
+      const float4 yv = *reinterpret_cast<const float4*>(tF + i * LD + 4 * bj);
+      const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) a32[u * 4 + w] = fmaf(xa[u], ya[w], a32[u * 4 + w]);
+    }
+  }
+  __syncthreads();
+  store_gram_partial<RT>(a32, reinterpret_cast<double*>(tF), R, gpart, blockIdx.x);
+}
+
 template <int RT>
 __global__ void __launch_bounds__(kT, 2) colnorm_rows(const float* __restrict__ N,
                                                    const float* __restrict__ W32, int64_t rows, int R,
@@ -1478,11 +1674,72 @@ dfacto_status dual_pass(dfacto_t* h);  // dual.cu: T110, T101, T011, T111
 
 namespace {
 
+// One GD step for R <= 32 with the fused row passes (gd_rows, gd_update_gram).
+template <typename T, int RT>
+dfacto_status gd_step_rows(dfacto_t* h) {
+  const int R = h->R;
+  cudaStream_t s = h->stream;
+  dfacto_status st;
+  for (int m = 0; m < 3; ++m)
+    if (!h->gram_valid[m] && (st = gram_of_factor(h, m)) != DFACTO_OK) return st;
+  DF_CUDA(h, cudaMemsetAsync(h->scal + kG2, 0, sizeof(double), s));
+  constexpr int LD = PassShape<RT>::LD;
+  const size_t smem_rows = sizeof(float) * ((size_t)RT * RT + 2 * (size_t)kT * LD);
+  const size_t smem_upd = sizeof(float) * 2 * (size_t)kT * LD;
+  allow_smem(gd_rows<T, RT>, smem_rows);
+  allow_smem(gd_update_gram<T, RT>, smem_upd);
+  for (int mode = 0; mode < 3; ++mode) {
+    const ModeCSR& M = h->m[mode];
+    hadamard_gamma<<<1, 256, 0, s>>>(h->gram[M.f], h->gram[M.in], R, h->lambda_reg, h->W, h->W32);
+    DF_COUNT();
+    if ((st = mttkrp_launch(h, mode, h->N)) != DFACTO_OK) return st;
+    const int64_t rows = M.dim_o;
+    const int nb = pass_blocks(rows);
+    const int64_t RR = (int64_t)R * R;
+    if ((st = grow_partials(h, 2 * nb * RR + 3 * nb)) != DFACTO_OK) return st;
+    double* gg = h->partials;
+    double* fg = h->partials + nb * RR;
+    double* sp = h->partials + 2 * nb * RR;
+    double* P = h->gd_mats + (size_t)mode * 3 * RR;
+    gd_rows<T, RT><<<nb, kT, smem_rows, s>>>(h->N, static_cast<const T*>(h->F[mode]), h->W32, rows, R,
+                                             h->grad[mode], gg, fg, sp);
+    DF_COUNT();
+    // P0 = F^T F (known), P1 = F^T G + G^T F, P2 = G^T G
+    DF_CUDA(h, cudaMemcpyAsync(P, h->gram[mode], sizeof(double) * RR, cudaMemcpyDeviceToDevice, s));
+    reduce_partials<<<(R * R + 31) / 32, kT, 0, s>>>(fg, nb, R * R, R, true, P + RR);
+    DF_COUNT();
+    reduce_partials<<<(R * R + 31) / 32, kT, 0, s>>>(gg, nb, R * R, R, false, P + 2 * RR);
+    DF_COUNT();
+    const int tlin = mode == 0 ? kT100 : (mode == 1 ? kT010 : kT001);
+    gd_scalars<<<1, kT, 0, s>>>(sp, nb, h->scal, tlin, mode == 0 ? kT000 : -1);
+    DF_COUNT();
+    DF_CUDA(h, cudaGetLastError());
+  }
+  if ((st = dual_pass(h)) != DFACTO_OK) return st;
+  gd_line_search<<<1, 256, 0, s>>>(h->gd_mats, R, h->lambda_reg, h->scal, h->flags + kFlagLsFail);
+  DF_COUNT();
+  for (int m = 0; m < 3; ++m) {
+    const int64_t rows = h->dims[m];
+    const int nb = pass_blocks(rows);
+    gd_update_gram<T, RT><<<nb, kT, smem_upd, s>>>(static_cast<T*>(h->F[m]), h->grad[m], h->scal,
+                                                  rows, R, h->partials);
+    DF_COUNT();
+    reduce_partials<<<(R * R + 31) / 32, kT, 0, s>>>(h->partials, nb, R * R, R, false, h->gram[m]);
+    DF_COUNT();
+    h->gram_valid[m] = true;
+  }
+  DF_CUDA(h, cudaGetLastError());
+  return DFACTO_OK;
+}
+
 template <typename T>
 dfacto_status gd_step_T(dfacto_t* h) {
   const int R = h->R;
   cudaStream_t s = h->stream;
   dfacto_status st;
+  if (R <= 8) return gd_step_rows<T, 8>(h);
+  if (R <= 16) return gd_step_rows<T, 16>(h);
+  if (R <= 32) return gd_step_rows<T, 32>(h);
   for (int m = 0; m < 3; ++m)
     if (!h->gram_valid[m] && (st = gram_of_factor(h, m)) != DFACTO_OK) return st;
   DF_CUDA(h, cudaMemsetAsync(h->scal + kG2, 0, sizeof(double), s));
