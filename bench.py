@@ -83,6 +83,9 @@ def parse_args():
     ap.add_argument("--mttkrp-only", action="store_true",
                     help="profiling driver: only the MTTKRP of each mode, --steps times, on the "
                          "workload scaled by --phi; prints per-mode times, no contract line")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="profiling driver: --steps graph-replayed sweeps of a batch workload "
+                         "(no autotuner, no job-by-job comparison); prints the mean sweep time")
     ap.add_argument("--als-only", action="store_true",
                     help="profiling driver: --steps ALS sweeps on the workload scaled by --phi; "
                          "prints the mean sweep time, no contract line")
@@ -677,6 +680,28 @@ def run_als_only(args):
                       "ms_per_sweep": e0.elapsed_time(e1) / max(args.steps, 1)}), flush=True)
 
 
+def run_batch_only(args):
+    """Mean sweep time of a batch workload (for profilers)."""
+    import torch
+
+    from paper_1406_4519_gb300 import dfacto
+    wl = BATCH_WORKLOADS[args.workload if args.workload in BATCH_WORKLOADS else "batch256"]
+    specs, jobs, alg = make_batch_jobs(wl, dfacto.BF16 if args.dtype == "bf16" else dfacto.F32,
+                                       torch.device("cuda"))
+    b = dfacto.Batch(jobs, autotune=False)
+    for _ in range(args.warmup):
+        b.als_iter(want_fits=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        b.als_iter(want_fits=False)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"jobs": len(jobs), "ms_per_sweep": e0.elapsed_time(e1) / max(args.steps, 1)}),
+          flush=True)
+    b.close()
+
+
 def run_mttkrp_only(args):
     """Per-mode MTTKRP timing on the workload scaled by phi (for profilers)."""
     import torch
@@ -719,6 +744,9 @@ def main():
         return
     if args.als_only:
         run_als_only(args)
+        return
+    if args.batch_only:
+        run_batch_only(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -1447,12 +1447,15 @@ __global__ void __launch_bounds__(kT) fit_from_parts_batch(const DenseJob* __res
 
 }  // namespace
 
-// Blocks of one job's row passes inside a batch: at least 1024 rows per block
-// (many jobs fill the GPU together; a block's fixed costs, the staging of
-// Gamma^{-1} and its R x R partial sums, are then paid per 1024 rows).
+// Blocks of one job's row passes inside a batch: at least 1024 * 32 / RT rows
+// per block (many jobs fill the GPU together; a block's fixed costs -- staging
+// Gamma^{-1}, its column and R x R partial sums -- are then paid per about
+// 32K row-columns of work; narrow rows get proportionally more rows).
 int dense_row_blocks(int64_t rows, int R) {
   if (R > 32) return (int)row_blocks(rows);
-  const int64_t b = (rows + 1023) / 1024;
+  const int RT = R <= 8 ? 8 : (R <= 16 ? 16 : 32);
+  const int64_t per = 1024 * 32 / RT;
+  const int64_t b = (rows + per - 1) / per;
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, kMaxBlocks));
 }
 
