@@ -83,6 +83,9 @@ def parse_args():
     ap.add_argument("--mttkrp-only", action="store_true",
                     help="profiling driver: only the MTTKRP of each mode, --steps times, on the "
                          "workload scaled by --phi; prints per-mode times, no contract line")
+    ap.add_argument("--gd-only", action="store_true",
+                    help="profiling driver: --steps GD steps on the workload scaled by --phi; "
+                         "prints the mean step time, no contract line")
     ap.add_argument("--batch-only", action="store_true",
                     help="profiling driver: --steps graph-replayed sweeps of a batch workload "
                          "(no autotuner, no job-by-job comparison); prints the mean sweep time")
@@ -680,6 +683,35 @@ def run_als_only(args):
                       "ms_per_sweep": e0.elapsed_time(e1) / max(args.steps, 1)}), flush=True)
 
 
+def run_gd_only(args):
+    """Mean GD step time on the workload scaled by phi (for profilers)."""
+    import torch
+
+    from paper_1406_4519_gb300 import dfacto, synth
+    wl = WORKLOADS[args.workload]
+    dims, nnz = scaled_replica(wl, args.phi)
+    if wl["zipf"]:
+        idx, val = synth.zipf_tensor(dims, nnz, wl["zipf"], seed=wl["seed"], device="cuda",
+                                     values=wl["values"], R_true=wl["R"])
+    else:
+        idx, val = synth.uniform_tensor(dims, nnz, seed=wl["seed"], device="cuda")
+    R = wl["R"]
+    t = dfacto.Tensor(idx, val, dims, rank=R,
+                      factor_dtype=dfacto.BF16 if args.dtype == "bf16" else dfacto.F32)
+    del idx, val
+    t.set_factors(synth.normal_factors(dims, R, seed=wl["seed"] + 1, device="cuda"))
+    for _ in range(args.warmup):
+        t.gd_iter(want=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        t.gd_iter(want=False)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"dims": dims, "nnz": nnz, "rank": R,
+                      "ms_per_step": e0.elapsed_time(e1) / max(args.steps, 1)}), flush=True)
+
+
 def run_batch_only(args):
     """Mean sweep time of a batch workload (for profilers)."""
     import torch
@@ -747,6 +779,9 @@ def main():
         return
     if args.batch_only:
         run_batch_only(args)
+        return
+    if args.gd_only:
+        run_gd_only(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
