@@ -66,12 +66,6 @@ unsigned grid_of(int64_t n) {
 
 size_t elem_bytes(int dtype) { return dtype == DFACTO_BF16 ? 2 : 4; }
 
-// Dynamic shared memory of the walk shape (VEC, G) at rank R (Walk2Shape).
-size_t walk_smem(int vec, int G, int R) {
-  const int segs = kWalkWarps * (32 / G);
-  const int U = std::min(G, 32 / vec);
-  return sizeof(float) * ((size_t)(2 * segs + 2 * kWalkWarps) * R + (size_t)kWalkWarps * 32 * U * vec);
-}
 
 int next_pow2(int x) {
   int p = 1;
@@ -315,7 +309,7 @@ dfacto_status batch_mttkrp_issue(dfacto_batch* b, int mode, cudaStream_t s,
         mp.shape[c] = C.shape;
         mp.cta_begin[c] = total;
         total += (int)C.ncta();
-        smem = std::max(smem, walk_smem(C.cfg.vec, C.cfg.G, C.R));
+        smem = std::max(smem, walk2_smem_bytes(C.cfg.vec, C.cfg.G, C.R));
       }
       mp.cta_begin[mp.nclass] = total;
       for (int c = mp.nclass + 1; c <= kMaxClasses; ++c) mp.cta_begin[c] = total;

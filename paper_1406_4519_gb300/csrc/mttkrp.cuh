@@ -433,21 +433,30 @@ __device__ __forceinline__ void smem_ld(const float* p, float (&v)[VEC]) {
 // slots when fibers are long; a sub-batch closes at most U).
 constexpr int kCloseChunk = 4;
 
+// Gathers in flight per lane of the walk shape (VEC, G): at most 16 gathered
+// values (U * VEC <= 16); more leave the kernel short of registers (spills) at
+// the budget of Walk2Shape.
+__host__ __device__ constexpr int walk2_gathers(int vec, int G) { return G < 16 / vec ? G : 16 / vec; }
+// Per-lane shared-memory slots for parked fiber sums.
+__host__ __device__ constexpr int walk2_park_slots(int vec, int G) { return walk2_gathers(vec, G); }
+// Dynamic shared memory of the walk at rank R: segment and warp partial rows
+// for the merge, then the park slots.
+inline size_t walk2_smem_bytes(int vec, int G, int R) {
+  return sizeof(float) * ((size_t)(2 * kWalkWarps * (32 / G) + 2 * kWalkWarps) * R +
+                          (size_t)kWalkWarps * 32 * walk2_park_slots(vec, G) * vec);
+}
+
 template <typename T, int VEC, int G>
 struct Walk2Shape {
   static constexpr int NG = 32 / G;
   static constexpr int SEGS = kWalkWarps * NG;
-  // Gathers in flight per lane: at most 16 gathered values (U * VEC <= 16);
-  // more leave the kernel short of registers (spills) at the budget below.
-  static constexpr int U = (G < 16 / VEC) ? G : (16 / VEC);
+  static constexpr int U = walk2_gathers(VEC, G);
   // Resident CTAs per SM the register budget is cut for: the kernel is bound by
   // the latency of its gathers and its L1 traffic, so occupancy pays more than
   // a few registers: 80 registers (3 CTAs) for eight-column lanes, 64 (4 CTAs)
   // for narrower ones.
   static constexpr int MIN_BLOCKS = VEC >= 8 ? 3 : 4;
-  static size_t smem_bytes(int R) {
-    return sizeof(float) * ((size_t)(2 * SEGS + 2 * kWalkWarps) * R + (size_t)kWalkWarps * 32 * U * VEC);
-  }
+  static size_t smem_bytes(int R) { return walk2_smem_bytes(VEC, G, R); }
 };
 
 // The walk of CTA `cta` of one MTTKRP (shared by the single-tensor kernel and
