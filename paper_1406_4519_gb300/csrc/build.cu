@@ -102,6 +102,19 @@ __global__ void make_keys_of(const int32_t* __restrict__ idx, int64_t nnz, int a
   }
 }
 
+// Chained run: key (o << bf) | f of the element at position p of the previous
+// mode's sorted order, whose permutation `chain` is carried along as payload.
+__global__ void make_keys_chain(const int32_t* __restrict__ idx, int64_t nnz, int ao, int af, int bf,
+                                const uint32_t* __restrict__ chain, uint64_t* __restrict__ key,
+                                uint32_t* __restrict__ perm) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+    const uint32_t t = chain[p];
+    key[p] = ((uint64_t)(uint32_t)idx[ao * nnz + t] << bf) | (uint32_t)idx[af * nnz + t];
+    perm[p] = t;
+  }
+}
+
 // Per-tile digit counts, written digit-major: cnt[d * ntiles + tile].
 __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __restrict__ key,
                                                           int64_t n, int shift,
@@ -396,7 +409,30 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
     }
   }
 
-  for (int mode = 0; mode < 3; ++mode) {
+  // Mode order of the sorts.  The sorted order of mode m is ascending in its
+  // row axis m, which is the column axis `in` of mode m - 1; a stable sort of
+  // that order by (o, f) alone therefore yields mode m - 1's full (o, f, in)
+  // order.  Only the first mode of the chain sorts the whole key; the start is
+  // the mode that minimises the total number of 8-bit digit passes.
+  int bits[3];
+  for (int a = 0; a < 3; ++a) bits[a] = nbits_for(h->dims[a]);
+  auto of_passes = [&](int m) { return (bits[m] + bits[(m + 2) % 3] + 7) / 8; };
+  auto full_passes = [&](int m) {
+    const int bo = bits[m], bf = bits[(m + 2) % 3], bi = bits[(m + 1) % 3];
+    return bo + bf + bi > 64 ? (bi + 7) / 8 + (bo + bf + 7) / 8 : (bo + bf + bi + 7) / 8;
+  };
+  int start = 2, best = 1 << 30;
+  for (int m = 2; m >= 0; --m) {
+    const int c = full_passes(m) + of_passes((m + 2) % 3) + of_passes((m + 1) % 3);
+    if (c < best) {
+      best = c;
+      start = m;
+    }
+  }
+  const uint32_t* chain = nullptr;  // permutation of the previous mode's sorted order
+
+  for (int step = 0; step < 3; ++step) {
+    const int mode = (start + 3 - step) % 3;
     ModeCSR& M = h->m[mode];
     M.o = mode;
     M.in = (mode + 1) % 3;
@@ -404,7 +440,9 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
     M.dim_o = h->dims[M.o];
     const int bo = nbits_for(h->dims[M.o]), bf = nbits_for(h->dims[M.f]),
               bi = nbits_for(h->dims[M.in]);
-    const bool wide = bo + bf + bi > 64;
+    const bool chained = chain != nullptr;
+    // wide: the sorted key holds (o, f) only and `in` is read through perm
+    const bool wide = chained || bo + bf + bi > 64;
     dfacto_status st = DFACTO_OK;
     st = dalloc(h, reinterpret_cast<void**>(&M.fiber_ptr), sizeof(int64_t) * (size_t)(M.dim_o + 1));
     if (st == DFACTO_OK) st = dalloc(h, reinterpret_cast<void**>(&M.nz_idx), sizeof(int32_t) * nn);
@@ -425,7 +463,17 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
       continue;
     }
     bool alt = false, alt2 = false;
-    if (!wide) {
+    const uint64_t* key = nullptr;
+    const uint32_t* perm = nullptr;
+    if (chained) {
+      uint32_t* va = (chain == v0) ? v1 : v0;   // payload of the sort
+      uint32_t* vb = (chain == v0) ? v0 : v1;   // its ping-pong partner (chain is copied first)
+      make_keys_chain<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, bf, chain, k0, va); DF_COUNT();
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = radix_sort(k0, va, k1, vb, n, bo + bf, s, &alt);
+      key = alt ? k1 : k0;
+      perm = alt ? vb : va;
+    } else if (!wide) {
       make_keys64<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, M.in, bf, bi, k0, v0); DF_COUNT();
       e = cudaGetLastError();
       if (e == cudaSuccess) e = radix_sort(k0, v0, k1, v1, n, bo + bf + bi, s, &alt);
@@ -448,8 +496,11 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
       cleanup();
       return cuda_fail(h, e, "radix sort");
     }
-    const uint64_t* key = alt ? k1 : k0;
-    const uint32_t* perm = alt ? v1 : v0;
+    if (!chained) {
+      key = alt ? k1 : k0;
+      perm = alt ? v1 : v0;
+    }
+    chain = perm;
     segment_flags<<<grid_for(n), 256, 0, s>>>(key, perm, n, bi, wide, d_idx, M.in, d_val, head,
                                              M.nz_idx, M.nz_val, h->flags + kFlagDup); DF_COUNT();
     e = cudaGetLastError();
