@@ -946,6 +946,60 @@ __device__ __forceinline__ void tile_load(const float* __restrict__ M, int64_t t
   }
 }
 
+// tile_load issued as 16-byte asynchronous copies (cp.async, committed as one
+// group) for R % 4 == 0: the caller overlaps the copy of the next tile with
+// the work on the current one and waits with cp_async_wait<n>() (at most n
+// groups still in flight) followed by a barrier.
+template <int LD>
+__device__ __forceinline__ void tile_load_async(const float* __restrict__ M, int64_t t0, int nt,
+                                                int R, float* __restrict__ tile) {
+  const float* src = M + t0 * R;
+  const int total4 = (nt * R) >> 2;
+  for (int e4 = threadIdx.x; e4 < total4; e4 += kT) {
+    const int e = 4 * e4, r = e / R, c = e - r * R;
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + r * LD + c);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + e) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+// Shared memory of the double-buffered row passes: W (RT x RT) and two tiles.
+template <int RT>
+constexpr size_t row_pass_smem() {
+  return sizeof(float) * ((size_t)RT * RT + 2 * (size_t)kT * (RT + 4));
+}
+
+// Tile t of a row pass in buffer t & 1: for R % 4 == 0 the next tile's copy is
+// issued before this one is waited for; otherwise the tile is loaded here.
+// Callers issue the first tile (row_pass_prefetch) before their loop, and call
+// this after a barrier that ends all use of the other buffer.
+template <int LD>
+__device__ __forceinline__ void row_pass_prefetch(const float* __restrict__ M, int64_t r0, int64_t r1,
+                                                  int R, float* __restrict__ tiles) {
+  if ((R & 3) == 0 && r0 < r1) tile_load_async<LD>(M, r0, (int)min((int64_t)kT, r1 - r0), R, tiles);
+}
+template <int LD>
+__device__ __forceinline__ float* row_pass_tile(const float* __restrict__ M, int64_t t0, int64_t r1,
+                                                int R, float* __restrict__ tiles, int buf) {
+  float* tile = tiles + (size_t)buf * kT * LD;
+  if ((R & 3) == 0) {
+    const int64_t tn = t0 + kT;
+    if (tn < r1) {
+      tile_load_async<LD>(M, tn, (int)min((int64_t)kT, r1 - tn), R, tiles + (size_t)(buf ^ 1) * kT * LD);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+  } else {
+    tile_load<LD>(M, t0, (int)min((int64_t)kT, r1 - t0), R, tile);
+  }
+  return tile;
+}
+
 // Tile rows (already rounded to T) back to rows [t0, t0 + nt) of an R-column
 // matrix in storage type T, with coalesced 16-byte stores where the layout
 // allows (FP32: R % 4 == 0; BF16: R % 8 == 0).
@@ -1001,19 +1055,23 @@ __device__ __forceinline__ void colnorm_rows_body(const float* __restrict__ N,
   using PS = PassShape<RT>;
   constexpr int CW = PS::CW, LD = PS::LD;
   static_assert(LD >= RT + 1, "the tile doubles as the FP64 reduction area");
-  __shared__ __align__(16) float Ws[RT * RT];
-  __shared__ __align__(16) float tile[kT * LD];
+  extern __shared__ __align__(16) float row_smem[];  // row_pass_smem<RT>() bytes
+  float* Ws = row_smem;
+  float* tiles = row_smem + RT * RT;
   stage_w<RT>(W32, R, Ws);
-  for (int e = threadIdx.x; e < kT * LD; e += kT) tile[e] = 0.f;
+  for (int e = threadIdx.x; e < 2 * kT * LD; e += kT) tiles[e] = 0.f;
   int64_t r0, r1;
   block_rows(rows, vb, vgrid, r0, r1);
   float sq[RT];
 #pragma unroll
   for (int c = 0; c < RT; ++c) sq[c] = 0.f;
-  for (int64_t t0 = r0; t0 < r1; t0 += kT) {
+  __syncthreads();
+  row_pass_prefetch<LD>(N, r0, r1, R, tiles);
+  int buf = 0;
+  for (int64_t t0 = r0; t0 < r1; t0 += kT, buf ^= 1) {
     const int nt = (int)min((int64_t)kT, r1 - t0);
     __syncthreads();
-    tile_load<LD>(N, t0, nt, R, tile);
+    const float* tile = row_pass_tile<LD>(N, t0, r1, R, tiles, buf);
     __syncthreads();
     if ((int)threadIdx.x < nt) {
       float n[RT];
@@ -1032,7 +1090,7 @@ __device__ __forceinline__ void colnorm_rows_body(const float* __restrict__ N,
     }
   }
   __syncthreads();
-  float* red = tile;  // [kT][RT + 1]
+  float* red = tiles;  // [kT][RT + 1]
 #pragma unroll
   for (int c = 0; c < RT; ++c) red[threadIdx.x * (RT + 1) + c] = sq[c];
   __syncthreads();
@@ -1061,8 +1119,9 @@ __device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ 
                                                       double* __restrict__ ipart, int vb, int vgrid) {
   using PS = PassShape<RT>;
   constexpr int CW = PS::CW, LD = PS::LD, NB4 = PS::NB4, NBLK = PS::NBLK, NGRP = PS::NGRP;
-  __shared__ __align__(16) float Ws[RT * RT];
-  __shared__ __align__(16) float tile[kT * LD];
+  extern __shared__ __align__(16) float row_smem[];  // row_pass_smem<RT>() bytes
+  float* Ws = row_smem;
+  float* tiles = row_smem + RT * RT;
   __shared__ float s_sc[RT], s_lm[RT];
   __shared__ double red[kT];
   stage_w<RT>(W32, R, Ws);
@@ -1070,7 +1129,7 @@ __device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ 
     s_sc[c] = c < R ? inv[c] : 0.f;
     s_lm[c] = (with_ip && c < R) ? (float)lambda[c] : 0.f;
   }
-  for (int e = threadIdx.x; e < kT * LD; e += kT) tile[e] = 0.f;
+  for (int e = threadIdx.x; e < 2 * kT * LD; e += kT) tiles[e] = 0.f;
   const int blk = threadIdx.x % NBLK, grp = threadIdx.x / NBLK;
   const int bi = blk / NB4, bj = blk % NB4;
   float a32[16];
@@ -1079,10 +1138,13 @@ __device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ 
   double ip = 0.0;
   int64_t r0, r1;
   block_rows(rows, vb, vgrid, r0, r1);
-  for (int64_t t0 = r0; t0 < r1; t0 += kT) {
+  __syncthreads();
+  row_pass_prefetch<LD>(N, r0, r1, R, tiles);
+  int buf = 0;
+  for (int64_t t0 = r0; t0 < r1; t0 += kT, buf ^= 1) {
     const int nt = (int)min((int64_t)kT, r1 - t0);
     __syncthreads();
-    tile_load<LD>(N, t0, nt, R, tile);
+    float* tile = row_pass_tile<LD>(N, t0, r1, R, tiles, buf);
     __syncthreads();
     float ip32 = 0.f;
     float* trow = tile + threadIdx.x * LD;
@@ -1135,7 +1197,7 @@ __device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ 
   // Add the groups of each block in group order, four entries at a time
   // through the tile ([kT][4] doubles = 8 KB <= the tile's kT * LD floats).
   __syncthreads();
-  double* rsm = reinterpret_cast<double*>(tile);
+  double* rsm = reinterpret_cast<double*>(tiles);
   for (int q0 = 0; q0 < 16; q0 += 4) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) rsm[threadIdx.x * 4 + q] = (double)a32[q0 + q];
@@ -1350,6 +1412,15 @@ __global__ void __launch_bounds__(kT, 2) gd_update_gram(T* __restrict__ F, const
   store_gram_partial<RT>(a32, reinterpret_cast<double*>(tF), R, gpart, blockIdx.x);
 }
 
+// Opt a kernel in to `bytes` of dynamic shared memory (above the default
+// 48 KB), once per kernel; later calls return the first call's result.
+template <auto Kernel, size_t Bytes>
+cudaError_t opt_in_smem() {
+  static const cudaError_t e =
+      cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Bytes);
+  return e;
+}
+
 template <int RT>
 __global__ void __launch_bounds__(kT, 2) colnorm_rows(const float* __restrict__ N,
                                                    const float* __restrict__ W32, int64_t rows, int R,
@@ -1541,12 +1612,15 @@ dfacto_status als_post_rows(dfacto_t* h, int mode, float* N) {
   const int64_t rows = h->m[mode].dim_o;
   const int nb = pass_blocks(rows);
   const bool last = (mode == 2);
-  colnorm_rows<RT><<<nb, kT, 0, s>>>(N, h->W32, rows, R, h->partials);
+  constexpr size_t smem = row_pass_smem<RT>();
+  DF_CUDA(h, (opt_in_smem<colnorm_rows<RT>, smem>()));
+  DF_CUDA(h, (opt_in_smem<scale_store_rows<T, RT>, smem>()));
+  colnorm_rows<RT><<<nb, kT, smem, s>>>(N, h->W32, rows, R, h->partials);
   DF_COUNT();
   finish_lambda<<<R, kT, 0, s>>>(h->partials, nb, R, h->lambda, h->inv_lambda);
   DF_COUNT();
-  scale_store_rows<T, RT><<<nb, kT, 0, s>>>(N, h->W32, h->inv_lambda, h->lambda, rows, R,
-                                            static_cast<T*>(h->F[mode]), h->partials, last, h->ipart);
+  scale_store_rows<T, RT><<<nb, kT, smem, s>>>(N, h->W32, h->inv_lambda, h->lambda, rows, R,
+                                               static_cast<T*>(h->F[mode]), h->partials, last, h->ipart);
   DF_COUNT();
   reduce_partials<<<(R * R + 31) / 32, kT, 0, s>>>(h->partials, nb, R * R, R, false, h->gram[mode]);
   DF_COUNT();
@@ -1807,20 +1881,26 @@ cudaError_t batch_gamma_inverse(const DenseJob* jobs, int n, int R, cudaStream_t
 
 namespace {
 template <int RT>
-void batch_post_rows(const DenseJob* jobs, const int32_t* begin, int n, int total_blocks, int R,
-                     int dtype, bool last, cudaStream_t s) {
-  colnorm_rows_batch<RT><<<total_blocks, kT, 0, s>>>(jobs, begin, n, R);
+cudaError_t batch_post_rows(const DenseJob* jobs, const int32_t* begin, int n, int total_blocks,
+                            int R, int dtype, bool last, cudaStream_t s) {
+  constexpr size_t smem = row_pass_smem<RT>();
+  cudaError_t e = opt_in_smem<colnorm_rows_batch<RT>, smem>();
+  if (e == cudaSuccess) e = opt_in_smem<scale_store_rows_batch<__nv_bfloat16, RT>, smem>();
+  if (e == cudaSuccess) e = opt_in_smem<scale_store_rows_batch<float, RT>, smem>();
+  if (e != cudaSuccess) return e;
+  colnorm_rows_batch<RT><<<total_blocks, kT, smem, s>>>(jobs, begin, n, R);
   DF_COUNT();
   finish_lambda_batch<<<n * R, kT, 0, s>>>(jobs, R);
   DF_COUNT();
   if (dtype == DFACTO_BF16)
-    scale_store_rows_batch<__nv_bfloat16, RT><<<total_blocks, kT, 0, s>>>(jobs, begin, n, R, last);
+    scale_store_rows_batch<__nv_bfloat16, RT><<<total_blocks, kT, smem, s>>>(jobs, begin, n, R, last);
   else
-    scale_store_rows_batch<float, RT><<<total_blocks, kT, 0, s>>>(jobs, begin, n, R, last);
+    scale_store_rows_batch<float, RT><<<total_blocks, kT, smem, s>>>(jobs, begin, n, R, last);
   DF_COUNT();
   const int per_job = (R * R + 31) / 32;
   reduce_partials_batch<<<n * per_job, kT, 0, s>>>(jobs, R, per_job);
   DF_COUNT();
+  return cudaGetLastError();
 }
 }  // namespace
 
@@ -1828,10 +1908,9 @@ cudaError_t batch_als_post(const DenseJob* jobs, const int32_t* begin, int n, in
                            int dtype, bool last, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (R <= 32) {
-    if (R <= 8) batch_post_rows<8>(jobs, begin, n, total_blocks, R, dtype, last, s);
-    else if (R <= 16) batch_post_rows<16>(jobs, begin, n, total_blocks, R, dtype, last, s);
-    else batch_post_rows<32>(jobs, begin, n, total_blocks, R, dtype, last, s);
-    return cudaGetLastError();
+    if (R <= 8) return batch_post_rows<8>(jobs, begin, n, total_blocks, R, dtype, last, s);
+    if (R <= 16) return batch_post_rows<16>(jobs, begin, n, total_blocks, R, dtype, last, s);
+    return batch_post_rows<32>(jobs, begin, n, total_blocks, R, dtype, last, s);
   }
   const int R4 = (R + 3) / 4;
   const size_t smem_a = solve_bytes(R);
