@@ -10,8 +10,15 @@
 // The sort is a least-significant-digit radix sort with 8-bit digits written
 // for this library: per-tile digit histograms, a device-wide scan, and a stable
 // scatter that ranks equal digits inside a warp with __match_any_sync.  Keys
-// of up to 64 bits sort in one run; wider (o, f, in) keys take two stable runs
-// (first by `in`, then by (o, f)).
+// of up to 64 bits sort in one run with the nonzero's value as payload; wider
+// (o, f, in) keys take two stable runs (first by `in`, then by (o, f)) with
+// the nonzero's position as payload.
+//
+// The three modes are sorted as a chain.  Mode m's sorted order ascends in its
+// row axis m, which is the `in` axis of mode m - 1, so a stable sort of that
+// order by (o, f) alone yields mode m - 1's (o, f, in) order.  For 64-bit keys
+// the next mode's key is a bit rotation of the sorted key (every axis is in
+// it), and its sort skips the low `in` bits.
 #include <algorithm>
 
 #include "device.cuh"
@@ -70,15 +77,33 @@ __global__ void sum_partials(const double* __restrict__ part, int n, double* __r
   }
 }
 
-// Composite key for keys that fit in 64 bits: (o << (bf + bi)) | (f << bi) | in.
-__global__ void make_keys64(const int32_t* __restrict__ idx, int64_t nnz, int ao, int af, int ai,
-                            int bf, int bi, uint64_t* __restrict__ key, uint32_t* __restrict__ perm) {
+__device__ __forceinline__ uint64_t shl64(uint64_t x, int b) { return b >= 64 ? 0ull : x << b; }
+__device__ __forceinline__ uint64_t shr64(uint64_t x, int b) { return b >= 64 ? 0ull : x >> b; }
+__device__ __forceinline__ uint64_t low64(uint64_t x, int b) { return b >= 64 ? x : x & ((1ull << b) - 1ull); }
+
+// Composite 64-bit key (o << (bf + bi)) | (f << bi) | in with the value's bits
+// as payload.
+__global__ void make_keys64_val(const int32_t* __restrict__ idx, const float* __restrict__ val,
+                                int64_t nnz, int ao, int af, int ai, int bf, int bi,
+                                uint64_t* __restrict__ key, uint32_t* __restrict__ vbits) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += stride) {
     const uint64_t o = (uint32_t)idx[ao * nnz + t], f = (uint32_t)idx[af * nnz + t],
                    in = (uint32_t)idx[ai * nnz + t];
-    key[t] = ((bf + bi >= 64) ? 0ull : (o << (bf + bi))) | (f << bi) | in;
-    perm[t] = (uint32_t)t;
+    key[t] = shl64(o, bf + bi) | shl64(f, bi) | in;
+    vbits[t] = __float_as_uint(val[t]);
+  }
+}
+
+// Key of the next mode of the chain from a sorted key of this one (in place):
+// (o, f, in) with widths (bo, bf, bi) becomes (f, in, o), i.e. the next mode's
+// (o, f, in) with widths (bf, bi, bo).
+__global__ void rotate_keys(uint64_t* __restrict__ key, int64_t n, int bo, int bf, int bi) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    const uint64_t k = key[p];
+    const uint64_t o = shr64(k, bf + bi), f = low64(shr64(k, bi), bf), in = low64(k, bi);
+    key[p] = shl64(f, bi + bo) | shl64(in, bo) | o;
   }
 }
 
@@ -185,8 +210,11 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(
 // After the sort: fiber-start flags, duplicate detection, nz_idx and nz_val.
 // narrow: key = (o,f,in) packed with `in` in the low bi bits.
 // wide:   key = (o,f) packed; `in` comes from the COO through perm.
+// With val_payload the payload holds the value's bits (narrow keys), else the
+// nonzero's position in the COO.
 __global__ void segment_flags(const uint64_t* __restrict__ key, const uint32_t* __restrict__ perm,
-                              int64_t n, int bi, bool wide, const int32_t* __restrict__ idx, int ai,
+                              int64_t n, int bi, bool wide, bool val_payload,
+                              const int32_t* __restrict__ idx, int ai,
                               const float* __restrict__ val, int32_t* __restrict__ head,
                               int32_t* __restrict__ nz_idx, float* __restrict__ nz_val,
                               int32_t* __restrict__ dup_flag) {
@@ -194,15 +222,15 @@ __global__ void segment_flags(const uint64_t* __restrict__ key, const uint32_t* 
   bool dup = false;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
     const uint64_t k = key[p];
-    const int64_t t = perm[p];
+    const uint32_t pl = perm[p];
     int32_t in;
     uint64_t fkey;
     if (wide) {
-      in = idx[ai * n + t];
+      in = idx[ai * n + pl];
       fkey = k;
     } else {
-      in = (int32_t)(k & ((bi >= 64) ? ~0ull : ((1ull << bi) - 1ull)));
-      fkey = (bi >= 64) ? 0 : (k >> bi);
+      in = (int32_t)low64(k, bi);
+      fkey = shr64(k, bi);
     }
     int32_t h = 1;
     if (p > 0) {
@@ -220,7 +248,7 @@ __global__ void segment_flags(const uint64_t* __restrict__ key, const uint32_t* 
     }
     head[p] = h;
     nz_idx[p] = in;
-    nz_val[p] = val[t];
+    nz_val[p] = val_payload ? __uint_as_float(pl) : val[pl];
   }
   if (__any_sync(kFull, dup) && (threadIdx.x & 31) == 0) atomicOr(dup_flag, 1);
 }
@@ -288,11 +316,13 @@ unsigned grid_for(int64_t n, int threads = 256, int64_t cap = 152 * 32) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, cap));
 }
 
-// Stable LSD radix sort of (key, val) pairs by bits [0, nbits).  The result is
-// left in (k0, v0) or (k1, v1); *in_alt tells which.
+// Stable LSD radix sort of (key, val) pairs by bits [lo_bit, hi_bit), digits
+// from lo_bit up (the order of keys equal in those bits is kept).  The result
+// is left in (k0, v0) or (k1, v1); *in_alt tells which.
 cudaError_t radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
-                       int nbits, cudaStream_t s, bool* in_alt) {
+                       int lo_bit, int hi_bit, cudaStream_t s, bool* in_alt) {
   *in_alt = false;
+  const int nbits = hi_bit - lo_bit;
   if (n <= 1 || nbits <= 0) return cudaSuccess;
   const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
   int32_t* cnt = nullptr;
@@ -303,7 +333,7 @@ cudaError_t radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, i
   uint64_t *ki = k0, *ko = k1;
   uint32_t *vi = v0, *vo = v1;
   for (int pass = 0; pass < passes && e == cudaSuccess; ++pass) {
-    const int shift = 8 * pass;
+    const int shift = lo_bit + 8 * pass;
     radix_hist<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n, shift, cnt, ntiles); DF_COUNT();
     e = cudaGetLastError();
     if (e == cudaSuccess) e = exclusive_scan_i32(cnt, cnt, kDigits * ntiles, s);
@@ -409,17 +439,17 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
     }
   }
 
-  // Mode order of the sorts.  The sorted order of mode m is ascending in its
-  // row axis m, which is the column axis `in` of mode m - 1; a stable sort of
-  // that order by (o, f) alone therefore yields mode m - 1's full (o, f, in)
-  // order.  Only the first mode of the chain sorts the whole key; the start is
-  // the mode that minimises the total number of 8-bit digit passes.
+  // Mode order of the sorts (the chain of the header): the start is the mode
+  // that minimises the total number of 8-bit digit passes; with 64-bit keys
+  // every start costs the same full sort, and each later mode sorts its o and
+  // f bits only.
   int bits[3];
   for (int a = 0; a < 3; ++a) bits[a] = nbits_for(h->dims[a]);
+  const bool narrow = bits[0] + bits[1] + bits[2] <= 64;
   auto of_passes = [&](int m) { return (bits[m] + bits[(m + 2) % 3] + 7) / 8; };
   auto full_passes = [&](int m) {
     const int bo = bits[m], bf = bits[(m + 2) % 3], bi = bits[(m + 1) % 3];
-    return bo + bf + bi > 64 ? (bi + 7) / 8 + (bo + bf + 7) / 8 : (bo + bf + bi + 7) / 8;
+    return narrow ? (bo + bf + bi + 7) / 8 : (bi + 7) / 8 + (bo + bf + 7) / 8;
   };
   int start = 2, best = 1 << 30;
   for (int m = 2; m >= 0; --m) {
@@ -429,7 +459,10 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
       start = m;
     }
   }
-  const uint32_t* chain = nullptr;  // permutation of the previous mode's sorted order
+  // The previous mode's sorted (key, payload) arrays and key widths.
+  uint64_t* prev_k = nullptr;
+  uint32_t* prev_v = nullptr;
+  int prev_bo = 0, prev_bf = 0, prev_bi = 0;
 
   for (int step = 0; step < 3; ++step) {
     const int mode = (start + 3 - step) % 3;
@@ -440,9 +473,10 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
     M.dim_o = h->dims[M.o];
     const int bo = nbits_for(h->dims[M.o]), bf = nbits_for(h->dims[M.f]),
               bi = nbits_for(h->dims[M.in]);
-    const bool chained = chain != nullptr;
-    // wide: the sorted key holds (o, f) only and `in` is read through perm
-    const bool wide = chained || bo + bf + bi > 64;
+    const bool chained = prev_k != nullptr;
+    // wide: the sorted key holds (o, f) only, the payload is the COO position
+    // and `in` and the value are read through it
+    const bool wide = !narrow;
     dfacto_status st = DFACTO_OK;
     st = dalloc(h, reinterpret_cast<void**>(&M.fiber_ptr), sizeof(int64_t) * (size_t)(M.dim_o + 1));
     if (st == DFACTO_OK) st = dalloc(h, reinterpret_cast<void**>(&M.nz_idx), sizeof(int32_t) * nn);
@@ -463,46 +497,66 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
       continue;
     }
     bool alt = false, alt2 = false;
-    const uint64_t* key = nullptr;
-    const uint32_t* perm = nullptr;
+    // The sort runs on (kin, vin) with (kalt, valt) as its ping-pong partner.
+    uint64_t* kin = k0;
+    uint32_t* vin = v0;
     if (chained) {
-      uint32_t* va = (chain == v0) ? v1 : v0;   // payload of the sort
-      uint32_t* vb = (chain == v0) ? v0 : v1;   // its ping-pong partner (chain is copied first)
-      make_keys_chain<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, bf, chain, k0, va); DF_COUNT();
+      kin = prev_k;
+      vin = prev_v;
+    }
+    uint64_t* kalt = (kin == k0) ? k1 : k0;
+    uint32_t* valt = (vin == v0) ? v1 : v0;
+    if (narrow && !chained) {
+      make_keys64_val<<<grid_for(n), 256, 0, s>>>(d_idx, d_val, n, M.o, M.f, M.in, bf, bi, kin, vin);
+      DF_COUNT();
       e = cudaGetLastError();
-      if (e == cudaSuccess) e = radix_sort(k0, va, k1, vb, n, bo + bf, s, &alt);
-      key = alt ? k1 : k0;
-      perm = alt ? vb : va;
-    } else if (!wide) {
-      make_keys64<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, M.in, bf, bi, k0, v0); DF_COUNT();
+      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, 0, bo + bf + bi, s, &alt);
+    } else if (narrow) {
+      // the previous order ascends in this mode's `in`: sort bits [bi, bi + bf + bo)
+      rotate_keys<<<grid_for(n), 256, 0, s>>>(kin, n, prev_bo, prev_bf, prev_bi);
+      DF_COUNT();
       e = cudaGetLastError();
-      if (e == cudaSuccess) e = radix_sort(k0, v0, k1, v1, n, bo + bf + bi, s, &alt);
+      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, bi, bo + bf + bi, s, &alt);
+    } else if (chained) {
+      // previous payload = COO positions in an order ascending in this mode's `in`
+      make_keys_chain<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, bf, vin, kalt, valt);
+      DF_COUNT();
+      e = cudaGetLastError();
+      std::swap(kin, kalt);
+      std::swap(vin, valt);
+      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, 0, bo + bf, s, &alt);
     } else {
-      make_keys_in<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.in, k0, v0); DF_COUNT();
+      make_keys_in<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.in, kin, vin); DF_COUNT();
       e = cudaGetLastError();
-      if (e == cudaSuccess) e = radix_sort(k0, v0, k1, v1, n, bi, s, &alt);
-      uint64_t* kk = alt ? k1 : k0;
-      uint32_t* vv = alt ? v1 : v0;
-      uint64_t* ko = alt ? k0 : k1;
-      uint32_t* vo = alt ? v0 : v1;
+      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, 0, bi, s, &alt);
+      if (alt) {
+        std::swap(kin, kalt);
+        std::swap(vin, valt);
+      }
       if (e == cudaSuccess) {
-        make_keys_of<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, bf, vv, kk); DF_COUNT();
+        make_keys_of<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, bf, vin, kin); DF_COUNT();
         e = cudaGetLastError();
       }
-      if (e == cudaSuccess) e = radix_sort(kk, vv, ko, vo, n, bo + bf, s, &alt2);
-      alt = alt ^ alt2;
+      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, 0, bo + bf, s, &alt2);
+      alt = alt2;
     }
     if (e != cudaSuccess) {
       cleanup();
       return cuda_fail(h, e, "radix sort");
     }
-    if (!chained) {
-      key = alt ? k1 : k0;
-      perm = alt ? v1 : v0;
+    if (alt) {
+      std::swap(kin, kalt);
+      std::swap(vin, valt);
     }
-    chain = perm;
-    segment_flags<<<grid_for(n), 256, 0, s>>>(key, perm, n, bi, wide, d_idx, M.in, d_val, head,
-                                             M.nz_idx, M.nz_val, h->flags + kFlagDup); DF_COUNT();
+    const uint64_t* key = kin;
+    const uint32_t* perm = vin;
+    prev_k = kin;
+    prev_v = vin;
+    prev_bo = bo;
+    prev_bf = bf;
+    prev_bi = bi;
+    segment_flags<<<grid_for(n), 256, 0, s>>>(key, perm, n, bi, wide, narrow, d_idx, M.in, d_val,
+                                             head, M.nz_idx, M.nz_val, h->flags + kFlagDup); DF_COUNT();
     e = cudaGetLastError();
     if (e == cudaSuccess) e = exclusive_scan_i32(head, fid, n, s);
     int32_t last[2] = {0, 0};

@@ -95,6 +95,16 @@ def test_csr_zipf_bit_exact():
     check_csr(t, idx, val, dims)
 
 
+def test_csr_64_bit_keys_bit_exact():
+    """21 + 21 + 22 = 64 key bits: the widest keys of the one-run sort, whose
+    chained modes rotate all 64 bits."""
+    dims = [2 ** 21, 2 ** 21, 2 ** 22]
+    idx, val = synth.zipf_tensor(dims, 50000, [1.2, 1.1, 1.3], seed=7, device="cuda",
+                                 values="lognormal")
+    t = dfacto.Tensor(idx, val, dims, rank=2)
+    check_csr(t, idx, val, dims)
+
+
 def test_csr_wide_keys_bit_exact():
     """Coordinates needing more than 64 key bits take the two-run sort."""
     dims = [2 ** 23, 2 ** 22, 2 ** 21]  # 23 + 22 + 21 = 66 bits
