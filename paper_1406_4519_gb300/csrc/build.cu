@@ -149,12 +149,18 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __res
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   const int lane = threadIdx.x & 31;
+  // all of the thread's keys first (independent loads in flight together)
+  int dg[kSortRounds];
+#pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-    const bool ok = i < n;
-    const int d = ok ? (int)((key[i] >> shift) & 0xff) : kDigits;
+    dg[r] = i < n ? (int)((key[i] >> shift) & 0xff) : kDigits;
+  }
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int d = dg[r];
     const unsigned peers = __match_any_sync(kFull, d);
-    if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[d], __popc(peers));
+    if (d < kDigits && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[d], __popc(peers));
   }
   __syncthreads();
   cnt[(int64_t)threadIdx.x * ntiles + blockIdx.x] = s_cnt[threadIdx.x];
@@ -173,11 +179,20 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(
   const unsigned lt = (1u << lane) - 1u;
   s_run[threadIdx.x] = ofs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  // the next round's element is loaded while this round is ranked
+  int64_t i_next = base + threadIdx.x;
+  uint64_t k_next = i_next < n ? kin[i_next] : 0;
+  uint32_t v_next = i_next < n ? vin[i_next] : 0;
   for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    const int64_t i = i_next;
     const bool ok = i < n;
-    const uint64_t k = ok ? kin[i] : 0;
-    const uint32_t v = ok ? vin[i] : 0;
+    const uint64_t k = k_next;
+    const uint32_t v = v_next;
+    i_next = i + kSortThreads;
+    if (r + 1 < kSortRounds && i_next < n) {
+      k_next = kin[i_next];
+      v_next = vin[i_next];
+    }
     const int d = ok ? (int)((k >> shift) & 0xff) : kDigits;
     const unsigned peers = __match_any_sync(kFull, d);
     const int rank = __popc(peers & lt);
