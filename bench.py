@@ -47,6 +47,32 @@ WORKLOADS = {
                       dims=[6_500_000, 2_500_000, 1_500_000], nnz=1_200_000_000,
                       zipf=[1.1, 1.3, 1.2], values="lognormal", R=10, seed=14064522),
 }
+L2_BYTES = 128 * 1024 * 1024  # the GPU's L2 (129 MB), rounded to a power of two
+
+# The paper's own synthetic sets (Sec. 5, Tables 4 and 5): preferential-attachment
+# coordinates, I = J = K = 10^e, nnz = 10^6 (Table 4) or 2I (Table 5); U(0,1)
+# values, R = 10 (the paper does not state R), N(0,1) starting factors.
+for _e in (4, 5, 6, 7):
+    _I = 10 ** _e
+    WORKLOADS["pa1M_1e%d" % _e] = dict(
+        desc="preferential attachment %dx%dx%d, 1M unique nnz, U(0,1) values, R=10, N(0,1) init"
+             % (_I, _I, _I), dims=[_I] * 3, nnz=1_000_000, zipf=None, pa=True, values="uniform",
+        R=10, seed=14064530 + _e)
+    WORKLOADS["pa2I_1e%d" % _e] = dict(
+        desc="preferential attachment %dx%dx%d, %d unique nnz (2I), U(0,1) values, R=10, "
+             "N(0,1) init" % (_I, _I, _I, 2 * _I), dims=[_I] * 3, nnz=2 * _I, zipf=None, pa=True,
+        values="uniform", R=10, seed=14064540 + _e)
+
+
+def make_tensor(wl, dims, nnz, device):
+    """The workload's seeded COO (int32 [3, nnz], float32 [nnz]) at the given size."""
+    from paper_1406_4519_gb300 import synth
+    if wl.get("pa"):
+        return synth.preferential_attachment_tensor(dims, nnz, seed=wl["seed"], device=device)
+    if wl["zipf"]:
+        return synth.zipf_tensor(dims, nnz, wl["zipf"], seed=wl["seed"], device=device,
+                                 values=wl["values"], R_true=wl["R"])
+    return synth.uniform_tensor(dims, nnz, seed=wl["seed"], device=device)
 # Batch of independent jobs: job shapes from synth.batch_job_specs (dims
 # log-uniform in [1e3, 2e5], nnz lognormal(ln 5e5, 1) clipped to [1e4, 5e6],
 # R uniform over {8, 16, 32}), uniform coordinates, U(0,1) values.
@@ -202,11 +228,7 @@ def scaled_replica(wl, phi):
 def make_replica(wl, phi, device):
     from paper_1406_4519_gb300 import synth
     dims, nnz = scaled_replica(wl, phi)
-    if wl["zipf"]:
-        idx, val = synth.zipf_tensor(dims, nnz, wl["zipf"], seed=wl["seed"], device=device,
-                                     values=wl["values"], R_true=wl["R"])
-    else:
-        idx, val = synth.uniform_tensor(dims, nnz, seed=wl["seed"], device=device)
+    idx, val = make_tensor(wl, dims, nnz, device)
     F0 = [f.double().cpu().numpy() for f in
           synth.normal_factors(dims, wl["R"], seed=wl["seed"] + 1, device=device)]
     return dims, idx.cpu().numpy(), val.cpu().numpy(), F0
@@ -335,11 +357,7 @@ def run_ours(args, rank, world, local_rank):
         return max_over_ranks_of(x, world, dev)
 
     # -- input (seeded, synthetic, generated on the device) --------------------
-    if wl["zipf"]:
-        idx, val = synth.zipf_tensor(dims, wl["nnz"], wl["zipf"], seed=wl["seed"], device=dev,
-                                     values=wl["values"], R_true=wl["R"])
-    else:
-        idx, val = synth.uniform_tensor(dims, wl["nnz"], seed=wl["seed"], device=dev)
+    idx, val = make_tensor(wl, dims, wl["nnz"], dev)
     F0 = synth.normal_factors(dims, R, seed=wl["seed"] + 1, device=dev)
     uniq = [int(torch.unique(idx[m]).numel()) for m in range(3)]
     torch.cuda.synchronize()
@@ -354,6 +372,34 @@ def run_ours(args, rank, world, local_rank):
 
     sampler = ClockSampler(local_rank)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    # Working set of a step: the three CSR copies and the factors.  When it is
+    # not well above the 129 MB L2, every timed step starts from a flushed L2
+    # (a 512 MB buffer is written before it; the write is outside the events).
+    working = sum(8 * info.nnz + 16 * x for x in info.nfib) + elem * R * sum(dims)
+    flush = working < 4 * L2_BYTES
+    scrub = torch.empty(4 * L2_BYTES // 4, dtype=torch.float32, device=dev) if flush else None
+
+    def timed(fn, steps):
+        """Mean ms of fn() over `steps` calls on the stream (events around the
+        loop, or around each call after an L2 flush)."""
+        if not flush:
+            a, b = ev(), ev()
+            a.record(stream)
+            for _ in range(steps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / steps
+        total = 0.0
+        for _ in range(steps):
+            scrub.fill_(1.0)
+            a, b = ev(), ev()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            total += a.elapsed_time(b)
+        return total / steps
 
     # -- ALS: warm-up, then K timed sweeps -------------------------------------
     for _ in range(args.warmup):
@@ -363,16 +409,10 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     sampler.start()
     launches0 = dfacto.dfacto_launch_count()
-    e0, e1 = ev(), ev()
-    e0.record(stream)
-    for _ in range(args.steps):
-        t.als_iter(want_fit=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    als_ms = timed(lambda: t.als_iter(want_fit=False), args.steps)
     launches = dfacto.dfacto_launch_count() - launches0
     barrier()
     torch.cuda.synchronize()
-    als_ms = e0.elapsed_time(e1) / args.steps
     als_ms_max = max_over_ranks(als_ms)
     st, fit = t.als_iter(want_fit=True)
 
@@ -382,13 +422,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         tg.gd_iter(want=False)
     torch.cuda.synchronize()
-    g0, g1 = ev(), ev()
-    g0.record(stream)
-    for _ in range(args.steps):
-        tg.gd_iter(want=False)
-    g1.record(stream)
-    torch.cuda.synchronize()
-    gd_ms = g0.elapsed_time(g1) / args.steps
+    gd_ms = timed(lambda: tg.gd_iter(want=False), args.steps)
     st_gd, loss, alpha = tg.gd_iter(want=True)
     del tg
 
@@ -399,18 +433,16 @@ def run_ours(args, rank, world, local_rank):
         o = out[:dims[mode]]
         for _ in range(args.warmup):
             t.mttkrp(mode, o)
-        m0, m1 = ev(), ev()
-        m0.record(stream)
-        for _ in range(args.steps):
-            t.mttkrp(mode, o)
-        m1.record(stream)
-        torch.cuda.synchronize()
-        mode_ms.append(m0.elapsed_time(m1) / args.steps)
+        mode_ms.append(timed(lambda: t.mttkrp(mode, o), args.steps))
     sampler.stop()
     alg = algorithmic_bytes(info, uniq, dims, R, elem)
     peak, peak_kind = measured_peaks()
     achieved = sum(alg) / (sum(mode_ms) * 1e-3) / 1e9
     sha = kernel_sha()
+    # traffic: the committed ncu capture's DRAM bytes per launch, only for the
+    # zipf50M FP32 walk it was taken on and while the kernel sources are unchanged
+    traffic = traffic_from_profile(sha) if (args.workload == "zipf50M" and dtype == dfacto.F32) else None
+    dram_gbs = None if traffic is None else traffic / (sum(mode_ms) / 3 * 1e-3) / 1e9
 
     # -- end to end through the C ABI from pinned host buffers -------------------
     e2e = None
@@ -472,15 +504,19 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": wl["desc"], "dims": dims, "nnz": wl["nnz"], "rank": R,
                    "factor_storage": args.dtype, "nfib": list(info.nfib),
-                   "l2": "no flush: inputs (CSR ~%.1f GB) exceed the 129 MB L2" %
-                         (sum(8 * info.nnz + 16 * x for x in info.nfib) / 1e9),
+                   "l2": ("L2 flushed before every timed step (working set %.0f MB; a 512 MB "
+                          "buffer written outside the timed events)" % (working / 1e6)) if flush else
+                         ("no flush: inputs (CSR + factors ~%.1f GB) exceed the 129 MB L2" %
+                          (working / 1e9)),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic_from_profile(sha),
+                     "frac": achieved / peak, "traffic": traffic,
                      "kernel": "mttkrp_walk2 (+ carry fix-up), mean over the three modes",
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_mode": alg, "ms_per_mode": mode_ms,
-                     "gbs_per_mode": [b / (m * 1e-3) / 1e9 for b, m in zip(alg, mode_ms)]},
+                     "gbs_per_mode": [b / (m * 1e-3) / 1e9 for b, m in zip(alg, mode_ms)],
+                     # the same time against the DRAM bytes ncu counted for the walk
+                     "dram_gbs": dram_gbs, "dram_frac": None if dram_gbs is None else dram_gbs / peak},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks,
         "gd_iter_per_s": 1e3 / gd_ms, "gd_ms": gd_ms, "gd_alpha": alpha, "gd_loss": loss,
@@ -661,11 +697,7 @@ def run_als_only(args):
     from paper_1406_4519_gb300 import dfacto, synth
     wl = WORKLOADS[args.workload]
     dims, nnz = scaled_replica(wl, args.phi)
-    if wl["zipf"]:
-        idx, val = synth.zipf_tensor(dims, nnz, wl["zipf"], seed=wl["seed"], device="cuda",
-                                     values=wl["values"], R_true=wl["R"])
-    else:
-        idx, val = synth.uniform_tensor(dims, nnz, seed=wl["seed"], device="cuda")
+    idx, val = make_tensor(wl, dims, nnz, "cuda")
     R = wl["R"]
     t = dfacto.Tensor(idx, val, dims, rank=R,
                       factor_dtype=dfacto.BF16 if args.dtype == "bf16" else dfacto.F32)
@@ -690,11 +722,7 @@ def run_gd_only(args):
     from paper_1406_4519_gb300 import dfacto, synth
     wl = WORKLOADS[args.workload]
     dims, nnz = scaled_replica(wl, args.phi)
-    if wl["zipf"]:
-        idx, val = synth.zipf_tensor(dims, nnz, wl["zipf"], seed=wl["seed"], device="cuda",
-                                     values=wl["values"], R_true=wl["R"])
-    else:
-        idx, val = synth.uniform_tensor(dims, nnz, seed=wl["seed"], device="cuda")
+    idx, val = make_tensor(wl, dims, nnz, "cuda")
     R = wl["R"]
     t = dfacto.Tensor(idx, val, dims, rank=R,
                       factor_dtype=dfacto.BF16 if args.dtype == "bf16" else dfacto.F32)
@@ -741,11 +769,7 @@ def run_mttkrp_only(args):
     from paper_1406_4519_gb300 import dfacto, synth
     wl = WORKLOADS[args.workload]
     dims, nnz = scaled_replica(wl, args.phi)
-    if wl["zipf"]:
-        idx, val = synth.zipf_tensor(dims, nnz, wl["zipf"], seed=wl["seed"], device="cuda",
-                                     values=wl["values"], R_true=wl["R"])
-    else:
-        idx, val = synth.uniform_tensor(dims, nnz, seed=wl["seed"], device="cuda")
+    idx, val = make_tensor(wl, dims, nnz, "cuda")
     R = wl["R"]
     F0 = synth.normal_factors(dims, R, seed=wl["seed"] + 1, device="cuda")
     t = dfacto.Tensor(idx, val, dims, rank=R,

@@ -14,6 +14,9 @@ measured on; the paper's real datasets are not available, these stand in):
 * ``zipf_tensor``     -- per-mode Zipf(s) coordinates (index 0 the most
   frequent), deduplicated to exactly ``nnz`` unique coordinates by redrawing;
   values either a planted CP model plus Gaussian noise, lognormal(0,1) or U(0,1).
+* ``preferential_attachment_tensor`` -- coordinates drawn one nonzero after
+  another, each axis index with probability proportional to (1 + the number of
+  nonzeros already at that index), values U(0,1).
 * ``normal_factors``  -- N(0,1) starting factors.
 
 Coordinates are returned as int32 [3, nnz] (rows i, j, k), values as float32,
@@ -28,7 +31,8 @@ import torch
 
 __all__ = [
     "generator", "zipf_cdf", "draw_zipf", "unique_coords", "uniform_tensor",
-    "zipf_tensor", "normal_factors", "batch_job_specs", "poisson_arrivals",
+    "zipf_tensor", "preferential_attachment_tensor", "normal_factors", "batch_job_specs",
+    "poisson_arrivals",
 ]
 
 
@@ -174,6 +178,69 @@ def zipf_tensor(dims: Sequence[int], nnz: int, exponents: Sequence[float], seed:
         val = torch.rand(nnz, generator=g, device=device, dtype=torch.float32)
     else:
         raise ValueError(values)
+    return ijk.to(torch.int32).contiguous(), val.contiguous()
+
+
+class _AttachmentAxis:
+    """One axis of the preferential-attachment process.
+
+    Draw t (0-based) takes index i with probability (c_i + 1) / (t + d), c_i
+    being the number of earlier draws at i: with probability d / (t + d) a
+    uniform index, otherwise the index of a uniformly chosen earlier draw (an
+    index with c_i earlier draws is copied with probability c_i / (t + d)).
+    ``extend(m)`` continues the process by m draws and returns their indices.
+    """
+
+    def __init__(self, d: int, g: torch.Generator, device):
+        self.d, self.g, self.device = int(d), g, device
+        self.drawn = torch.empty(0, dtype=torch.int64, device=device)
+
+    def extend(self, m: int) -> torch.Tensor:
+        t0 = self.drawn.numel()
+        t = torch.arange(t0, t0 + m, device=self.device, dtype=torch.int64)
+        u = torch.rand(m, generator=self.g, device=self.device, dtype=torch.float64)
+        fresh = u * (t + self.d).to(torch.float64) < self.d
+        uni = torch.randint(0, self.d, (m,), generator=self.g, device=self.device)
+        src = (torch.rand(m, generator=self.g, device=self.device, dtype=torch.float64)
+               * t.to(torch.float64)).to(torch.int64)
+        src = torch.minimum(src, (t - 1).clamp(min=0))
+        # a copy points at an earlier draw: earlier batches are resolved, draws
+        # of this batch are followed until they reach a uniform one
+        old = ~fresh & (src < t0)
+        val = torch.where(fresh, uni, torch.zeros_like(uni))
+        if t0 > 0:
+            val = torch.where(old, self.drawn[src.clamp(max=t0 - 1)], val)
+        local = torch.where(fresh | old, t, src) - t0
+        while True:
+            nxt = local[local]
+            if torch.equal(nxt, local):
+                break
+            local = nxt
+        out = val[local]
+        self.drawn = torch.cat([self.drawn, out])
+        return out
+
+
+def preferential_attachment_tensor(dims: Sequence[int], nnz: int, seed: int, device="cpu"
+                                   ) -> Tuple[torch.Tensor, torch.Tensor]:
+    """Skewed coordinates from a preferential-attachment process, values U(0,1).
+
+    Nonzeros are added one after another and the axes draw independently, so
+    the probability of (i, j, k) is the product of per-axis probabilities, each
+    proportional to 1 + the number of nonzeros already at that index (the +1
+    lets unused indices start).  Draws continue until ``nnz`` distinct
+    coordinates exist; repeated coordinates still count.  Returns (int32
+    [3, nnz] in a seeded random order, float32 [nnz]).
+    """
+    device = torch.device(device)
+    g = generator(seed, device)
+    axes = [_AttachmentAxis(int(d), g, device) for d in dims]
+
+    def sampler(m):
+        return torch.stack([a.extend(m) for a in axes])
+
+    ijk = _shuffle(unique_coords(dims, nnz, sampler, g, device), g, device)
+    val = torch.rand(nnz, generator=g, device=device, dtype=torch.float32)
     return ijk.to(torch.int32).contiguous(), val.contiguous()
 
 

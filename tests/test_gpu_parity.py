@@ -167,6 +167,28 @@ def test_mttkrp_power_law_rows_span_many_ctas(seg, walk):
         assert rel(host(t.mttkrp(mode)), oracle.mttkrp(ot, mode, Fh)) <= MTTKRP_TOL
 
 
+@pytest.mark.parametrize("dims,nnz", [([2000, 2000, 2000], 100000), ([20000, 20000, 20000], 40000)])
+def test_preferential_attachment_csr_mttkrp_and_sweep(dims, nnz):
+    """The paper's synthetic sets (Sec. 5): dense-ish (50 nonzeros per index,
+    rich-get-richer heads) and sparse (nnz = 2I, singleton fibers) draws; CSR
+    bit-exact, MTTKRP within the FP32 bar and one ALS sweep step-wise."""
+    idx, val = synth.preferential_attachment_tensor(dims, nnz, seed=17, device="cuda")
+    F = synth.normal_factors(dims, 10, seed=18, device="cuda")
+    t = dfacto.Tensor(idx, val, dims, rank=10)
+    t.set_factors(F)
+    check_csr(t, idx, val, dims)
+    ot = as_oracle(idx, val, dims)
+    Fh = [host(f) for f in F]
+    for mode in range(3):
+        assert rel(host(t.mttkrp(mode)), oracle.mttkrp(ot, mode, Fh)) <= MTTKRP_TOL, mode
+    st, fit = t.als_iter()
+    st_o, Fo, lam_o, fit_o = oracle.als_sweep(ot, Fh)
+    after = [host(f) for f in t.factors()]
+    for m in range(3):
+        assert rel(after[m], Fo[m]) <= 1e-4, m
+    assert abs(fit - fit_o) <= 1e-5
+
+
 def test_mttkrp_single_row_and_single_fiber():
     """All nonzeros in one output row (mode 0) and in one fiber (i, k fixed)."""
     J = 5000
