@@ -73,8 +73,11 @@ typedef enum dfacto_dtype {
  *                 must divide R); 0 lets the library choose.
  *   walk          MTTKRP kernel: 1 detects fiber ends from the fiber pointers
  *                 as it walks, 2 from a per-nonzero end bitmask and closes the
- *                 fibers of a few steps together; 0 lets the library choose.
- *                 Both compute the same sums in the same order.
+ *                 fibers of a few steps together, 3 stages the gathered factor
+ *                 rows in shared memory with bulk asynchronous copies (FP32
+ *                 factors with R % 4 == 0 and R <= 32; other shapes use 2);
+ *                 0 lets the library choose.  All compute the same sums in the
+ *                 same order.
  */
 typedef struct dfacto_options {
   int32_t rank;

@@ -134,6 +134,7 @@ dfacto_status read_back(dfacto_t* h) {
                              cudaMemcpyDeviceToHost, h->stream));
   DF_CUDA(h, cudaStreamSynchronize(h->stream));
   if (h->host_flags[kFlagInternal]) return fail(h, DFACTO_EINTERNAL, "internal consistency check failed");
+  if (h->host_flags[kFlagTimeout]) return fail(h, DFACTO_ETIMEOUT, "a device-side wait gave up");
   return DFACTO_OK;
 }
 
@@ -268,7 +269,7 @@ dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, co
   if (opt.vec != 0 && (opt.vec != 1 && opt.vec != 2 && opt.vec != 4 && opt.vec != 8)) return DFACTO_EINVAL;
   if (opt.vec != 0 && R % opt.vec != 0) return DFACTO_EINVAL;
   if (opt.seg_nnz < 0) return DFACTO_EINVAL;
-  if (opt.walk < 0 || opt.walk > 2) return DFACTO_EINVAL;
+  if (opt.walk < 0 || opt.walk > 3) return DFACTO_EINVAL;
 
   dfacto_t* h = new (std::nothrow) dfacto_handle();
   if (!h) return DFACTO_ENOMEM;
@@ -355,7 +356,18 @@ dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, co
   }
   for (int m = 0; m < 3; ++m) {
     h->m[m].cfg = choose_walk(R, h->dtype, nnz, h->m[m].nfib, opt.seg_nnz, opt.vec);
-    if (opt.walk > 0) h->m[m].cfg.kernel = opt.walk;
+    if (opt.walk == 3) {
+      // staged walk: one 32-lane group per segment, lane c on column c
+      // (shapes it does not take keep the bitmask walk)
+      WalkCfg& c = h->m[m].cfg;
+      c.kernel = stage_supported(h->dtype, R) ? 3 : 2;
+      if (c.kernel == 3) {
+        c.vec = 1;
+        c.G = 32;
+      }
+    } else if (opt.walk > 0) {
+      h->m[m].cfg.kernel = opt.walk;
+    }
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) return bail(DFACTO_ECUDA);
   *out = h;

@@ -18,7 +18,8 @@ struct WalkCfg {
   int vec = 0;    // columns per lane (1, 2, 4, 8)
   int G = 0;      // lanes per group (power of two, G * vec >= R)
   int seg = 0;    // nonzeros per segment (multiple of 32)
-  int kernel = 1; // 1: mttkrp_walk, 2: mttkrp_walk2 (fiber ends from a bitmask)
+  int kernel = 1; // 1: mttkrp_walk, 2: mttkrp_walk2 (fiber ends from a bitmask),
+                  // 3: mttkrp_stage (rows staged in shared memory by bulk copies)
 };
 
 constexpr int kWalkWarps = 8;  // warps per MTTKRP CTA
@@ -63,6 +64,7 @@ enum Flag : int {
   kFlagSingular,      // a pseudo-inverse was used
   kFlagLsFail,        // line search failed
   kFlagInternal,      // internal check failed
+  kFlagTimeout,       // a bounded device-side wait gave up
   kNumFlags
 };
 
@@ -144,6 +146,8 @@ dfacto_status ensure_segments(dfacto_t* h, int mode);
 
 // ---- MTTKRP (mttkrp*.cu) --------------------------------------------------
 WalkCfg choose_walk(int R, int dtype, int64_t nnz, int64_t nfib, int seg_opt, int vec_opt);
+// Shapes the staged walk (kernel 3) takes: FP32 factors, R % 4 == 0, R <= 32.
+bool stage_supported(int dtype, int R);
 dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out);
 
 // ---- batches (batch.cu, dense.cu) -----------------------------------------

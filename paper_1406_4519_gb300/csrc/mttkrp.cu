@@ -174,7 +174,9 @@ dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out) {
   if (ncta > 0) {
     const size_t smem = sizeof(float) * (size_t)(2 * segs + 2 * kWalkWarps) * h->R;
     cudaError_t e;
-    if (cfg.kernel == 2)
+    if (cfg.kernel == 3)
+      e = launch_walk_stage(a, ncta, h->flags + kFlagTimeout, h->stream);
+    else if (cfg.kernel == 2)
       e = (h->dtype == DFACTO_BF16) ? launch_walk2<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, h->stream)
                                     : launch_walk2<float>(cfg.vec, cfg.G, a, ncta, h->stream);
     else

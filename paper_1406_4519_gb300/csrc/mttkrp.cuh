@@ -713,4 +713,10 @@ cudaError_t launch_walk(int vec, int G, const MttkrpParams& a, int64_t ncta, siz
 template <typename T>
 cudaError_t launch_walk2(int vec, int G, const MttkrpParams& a, int64_t ncta, cudaStream_t s);
 
+// The staged walk (walk = 3, mttkrp_stage.cu): FP32 factors, R % 4 == 0,
+// R <= 32, one segment of a.seg (% 32 == 0) nonzeros per warp; a bounded wait
+// that gives up sets *timeout_flag.
+size_t stage_smem_bytes(int R);
+cudaError_t launch_walk_stage(const MttkrpParams& a, int64_t ncta, int32_t* timeout_flag, cudaStream_t s);
+
 }  // namespace dfacto
