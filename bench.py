@@ -445,6 +445,11 @@ def run_ours(args, rank, world, local_rank):
     dram_gbs = None if traffic is None else traffic / (sum(mode_ms) / 3 * 1e-3) / 1e9
 
     # -- end to end through the C ABI from pinned host buffers -------------------
+    # (the timed handle and torch's cached blocks are released first: the
+    # end-to-end build of the 1.2B-nonzero tensor needs ~90 GB of its own)
+    del t, out
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     e2e = None
     if not args.no_e2e:
         idx_h = idx.cpu().pin_memory()
