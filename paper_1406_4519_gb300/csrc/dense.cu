@@ -917,6 +917,9 @@ __device__ __forceinline__ void stage_w(const float* __restrict__ W32, int R, fl
 }
 
 // Output columns are produced CW = min(RT, 16) at a time (fewer live registers).
+// The Gram partials use NGRP groups of NBLK threads (one 4 x 4 block each);
+// when NBLK does not divide kT (RT = 12: 28 groups of 9) the last kT % NBLK
+// threads add nothing.
 template <int RT>
 struct PassShape {
   static constexpr int CW = RT < 16 ? RT : 16;
@@ -1180,7 +1183,7 @@ __device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ 
     ip += (double)ip32;
     __syncthreads();
     tile_store<LD>(tile, t0, nt, R, F);
-    for (int i = grp; i < nt; i += NGRP) {
+    for (int i = grp; grp < NGRP && i < nt; i += NGRP) {
       const float4 xv = *reinterpret_cast<const float4*>(tile + i * LD + 4 * bi);
       const float4 yv = *reinterpret_cast<const float4*>(tile + i * LD + 4 * bj);
       const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
@@ -1339,7 +1342,7 @@ __global__ void __launch_bounds__(kT, 2) gd_rows(const float* __restrict__ N, co
     for (int t = 0; t < 3; ++t) ad[t] += (double)af[t];
     __syncthreads();
     tile_store<LD>(tN, t0, nt, R, grad);
-    for (int i = grp; i < nt; i += NGRP) {
+    for (int i = grp; grp < NGRP && i < nt; i += NGRP) {
       const float4 gx = *reinterpret_cast<const float4*>(tN + i * LD + 4 * bi);
       const float4 gy = *reinterpret_cast<const float4*>(tN + i * LD + 4 * bj);
       const float4 fx = *reinterpret_cast<const float4*>(tF + i * LD + 4 * bi);
@@ -1398,7 +1401,7 @@ __global__ void __launch_bounds__(kT, 2) gd_update_gram(T* __restrict__ F, const
     }
     __syncthreads();
     tile_store<LD>(tF, t0, nt, R, F);
-    for (int i = grp; i < nt; i += NGRP) {
+    for (int i = grp; grp < NGRP && i < nt; i += NGRP) {
       const float4 xv = *reinterpret_cast<const float4*>(tF + i * LD + 4 * bi);
       const float4 yv = *reinterpret_cast<const float4*>(tF + i * LD + 4 * bj);
       const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
@@ -1524,7 +1527,7 @@ __global__ void __launch_bounds__(kT) fit_from_parts_batch(const DenseJob* __res
 // 32K row-columns of work; narrow rows get proportionally more rows).
 int dense_row_blocks(int64_t rows, int R) {
   if (R > 32) return (int)row_blocks(rows);
-  const int RT = R <= 8 ? 8 : (R <= 16 ? 16 : 32);
+  const int RT = R <= 8 ? 8 : (R <= 12 ? 12 : (R <= 16 ? 16 : 32));
   const int64_t per = 1024 * 32 / RT;
   const int64_t b = (rows + per - 1) / per;
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, kMaxBlocks));
@@ -1637,6 +1640,7 @@ dfacto_status als_post_T(dfacto_t* h, int mode, float* N) {
   const int R4 = (R + 3) / 4;
   cudaStream_t s = h->stream;
   if (R <= 8) return als_post_rows<T, 8>(h, mode, N);
+  if (R <= 12) return als_post_rows<T, 12>(h, mode, N);
   if (R <= 16) return als_post_rows<T, 16>(h, mode, N);
   if (R <= 32) return als_post_rows<T, 32>(h, mode, N);
   const int64_t rows = M.dim_o;
@@ -1815,6 +1819,7 @@ dfacto_status gd_step_T(dfacto_t* h) {
   cudaStream_t s = h->stream;
   dfacto_status st;
   if (R <= 8) return gd_step_rows<T, 8>(h);
+  if (R <= 12) return gd_step_rows<T, 12>(h);
   if (R <= 16) return gd_step_rows<T, 16>(h);
   if (R <= 32) return gd_step_rows<T, 32>(h);
   for (int m = 0; m < 3; ++m)
@@ -1909,6 +1914,7 @@ cudaError_t batch_als_post(const DenseJob* jobs, const int32_t* begin, int n, in
   if (n <= 0) return cudaSuccess;
   if (R <= 32) {
     if (R <= 8) return batch_post_rows<8>(jobs, begin, n, total_blocks, R, dtype, last, s);
+    if (R <= 12) return batch_post_rows<12>(jobs, begin, n, total_blocks, R, dtype, last, s);
     if (R <= 16) return batch_post_rows<16>(jobs, begin, n, total_blocks, R, dtype, last, s);
     return batch_post_rows<32>(jobs, begin, n, total_blocks, R, dtype, last, s);
   }

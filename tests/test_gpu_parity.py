@@ -403,15 +403,15 @@ def ray_tolerance(ot, F, G, alpha, lam_reg, eps=2e-6):
     return eps * (2 * T + Qabs + ridge) / 2 + 1e-9
 
 
+@pytest.mark.parametrize("R", [8, 10, 12])
 @pytest.mark.parametrize("lam_reg", [0.0, 0.5])
-def test_gd_stepwise(lam_reg):
+def test_gd_stepwise(lam_reg, R):
     """Each GD step from the GPU's state: the accepted alpha is the oracle's (the
     Armijo decisions coincide unless a trial sits within rounding of the
     threshold), the objective agrees within ray_tolerance and the new factors
     to 1e-5 normwise."""
     dims = [120, 90, 60]
-    R = 8
-    t, idx, val, F = make(dims, 8000, R, seed=700)
+    t, idx, val, F = make(dims, 8000, R, seed=700 + R)
     t = dfacto.Tensor(idx, val, dims, rank=R, lambda_reg=lam_reg)
     t.set_factors(F)
     ot = as_oracle(idx, val, dims)
