@@ -17,6 +17,10 @@ so that a burst of arrivals does not rebuild after every sweep; retirements
 alone only once the finished jobs, which ride along until then, hold
 `waste_limit` of the batch's nonzeros.
 
+A request whose tensor cannot be built (invalid coordinates, duplicates, no
+device memory) finishes at once with its error and no result; the others are
+not affected.
+
 The scheduling decisions live in `Scheduler` (pure Python, no GPU), the device
 work in `GpuEngine`; `serve()` runs the loop in real time against a list of
 arrival times.  `serve_sequential()` is the comparison: one job at a time, in
@@ -49,6 +53,7 @@ class JobState:
     fits: List[float] = field(default_factory=list)
     footprint: int = 0
     result: Optional[dict] = None
+    error: Optional[str] = None    # set when the request could not be served
 
     @property
     def latency(self) -> Optional[float]:
@@ -115,6 +120,14 @@ class Scheduler:
             else:
                 break
         return out
+
+    def reject(self, job: JobState, now: float, error: str) -> None:
+        """A pending job that cannot be served (its tensor failed to build): it
+        leaves the queue finished, with the error and no result."""
+        self.pending.remove(job)
+        job.error = error
+        job.finished_at = now
+        self.done.append(job)
 
     def admit(self, jobs: Sequence[JobState], now: float) -> None:
         for job in jobs:
@@ -231,10 +244,16 @@ def serve(jobs: Sequence[JobSpec], budget_bytes: float = 120e9, max_iters: int =
             nxt += 1
         adm = sch.admissible()
         if adm:
+            built = []
             for job in adm:
-                engine.build(job)
-            sch.admit(adm, clock() - t0)
-            changed = True
+                try:
+                    engine.build(job)
+                    built.append(job)
+                except Exception as e:  # a request that cannot be built fails alone
+                    sch.reject(job, clock() - t0, "%s: %s" % (type(e).__name__, e))
+            if built:
+                sch.admit(built, clock() - t0)
+                changed = True
         now = clock() - t0
         waste = (sum(sch_done_nnz[j] for j in retired_in_batch) / in_batch_nnz
                  if in_batch_nnz else 0.0)
@@ -296,10 +315,13 @@ def serve_sequential(jobs: Sequence[JobSpec], max_iters: int = 50, tol: float = 
 
 
 def latency_stats(done: Sequence[JobState]) -> dict:
-    """p50 / p99 latency and throughput of finished jobs."""
+    """p50 / p99 latency and throughput of the jobs that finished with a
+    result (requests that failed are counted apart)."""
+    failed = sum(1 for j in done if j.error is not None)
+    done = [j for j in done if j.error is None]
     lat = sorted(j.latency for j in done if j.latency is not None)
     if not lat:
-        return {"jobs": 0}
+        return {"jobs": 0, "failed": failed}
 
     def pct(p):
         k = min(len(lat) - 1, max(0, int(round(p / 100.0 * (len(lat) - 1)))))
@@ -307,7 +329,8 @@ def latency_stats(done: Sequence[JobState]) -> dict:
 
     first = min(j.spec.arrival for j in done)
     last = max(j.finished_at for j in done)
-    return {"jobs": len(lat), "p50_s": pct(50), "p99_s": pct(99), "mean_s": sum(lat) / len(lat),
+    return {"jobs": len(lat), "failed": failed, "p50_s": pct(50), "p99_s": pct(99),
+            "mean_s": sum(lat) / len(lat),
             "jobs_per_s": len(lat) / max(last - first, 1e-9),
             "mean_iters": sum(j.iters for j in done) / len(done),
             "mean_final_fit": sum(j.fits[-1] for j in done if j.fits) / max(1, len(done))}

@@ -157,6 +157,37 @@ def test_cap_applies_when_fit_keeps_moving():
     assert done[0].iters == 7
 
 
+class FailingEngine(FakeEngine):
+    """A FakeEngine whose build of the listed jobs raises (an unbuildable
+    request: out-of-range coordinates, duplicates, no memory)."""
+
+    def __init__(self, clock, rates, bad):
+        super().__init__(clock, rates)
+        self.bad = set(bad)
+
+    def build(self, job):
+        if job.spec.job_id in self.bad:
+            raise RuntimeError("cannot build job %d" % job.spec.job_id)
+        super().build(job)
+
+
+def test_a_request_that_fails_to_build_fails_alone():
+    clock = FakeClock()
+    rates = {i: 0.5 for i in range(5)}
+    eng = FailingEngine(clock, rates, bad=[1, 3])
+    fp = serve.footprint_bytes([100, 100, 100], 1000, 8, 2)
+    done = serve.serve(specs(5, [0.0, 0.0, 0.001, 0.002, 0.003]), engine=eng, clock=clock,
+                       sleep=clock.sleep, max_iters=50, tol=1e-4, budget_bytes=2.5 * fp)
+    by_id = {j.spec.job_id: j for j in done}
+    assert sorted(by_id) == [0, 1, 2, 3, 4]
+    for jid in (1, 3):
+        assert by_id[jid].error and by_id[jid].result is None and by_id[jid].iters == 0
+    for jid in (0, 2, 4):
+        assert by_id[jid].error is None and by_id[jid].iters == converge_sweep(0.5, 1e-4)
+    s = serve.latency_stats(done)
+    assert s["jobs"] == 3 and s["failed"] == 2
+
+
 def test_latency_stats():
     jobs = []
     for i, lat in enumerate([1.0, 2.0, 3.0, 4.0, 100.0]):
