@@ -95,6 +95,10 @@ def test_host_side_argument_checks(lib):
     opt = dfacto.dfacto_options_init(8, lambda_reg=-1.0)
     assert lib.dfacto_build(None, None, 0, dims, ctypes.byref(opt), None,
                             ctypes.byref(out)) == dfacto.EINVAL
+    for walk in (-1, 4):  # walks 0 (library's choice) to 3 exist
+        opt = dfacto.dfacto_options_init(8, walk=walk)
+        assert lib.dfacto_build(None, None, 0, dims, ctypes.byref(opt), None,
+                                ctypes.byref(out)) == dfacto.EINVAL
     assert out.value is None
     for fn in ("dfacto_mttkrp", "dfacto_als_iter", "dfacto_fit", "dfacto_sync"):
         args = {"dfacto_mttkrp": (None, 0, None), "dfacto_als_iter": (None, None),
