@@ -47,7 +47,7 @@ typedef enum dfacto_status {
                            definite and its pseudo-inverse was used              */
   DFACTO_ELSFAIL = 7,   /* GD line search found no acceptable step; the factors
                            are unchanged                                          */
-  DFACTO_ETIMEOUT = 8,  /* a bounded device-side wait gave up                     */
+  DFACTO_ETIMEOUT = 8,  /* reserved: no kernel of this version waits on another  */
   DFACTO_EINTERNAL = 9  /* an internal consistency check failed                   */
 } dfacto_status;
 
@@ -67,17 +67,16 @@ typedef enum dfacto_dtype {
  *                 the objective (GD): the regularized forms of Appendix B
  *                 (Eq. tensorapprx-ref-sol) and Appendix C (Eq. gd-obj-fn-reg).
  *                 Must be >= 0; 0 (the default) is the plain method.
- *   seg_nnz       nonzeros walked by one lane group in the MTTKRP kernel; 0
- *                 lets the library choose.  Rounded to a multiple of 32.
+ *   seg_nnz       nonzeros walked by one lane group in the MTTKRP kernel, at
+ *                 most 4096; 0 lets the library choose.  Rounded to a multiple
+ *                 of 32.
  *   vec           factor columns per lane in the MTTKRP kernel (1, 2, 4 or 8;
  *                 must divide R); 0 lets the library choose.
  *   walk          MTTKRP kernel: 1 detects fiber ends from the fiber pointers
  *                 as it walks, 2 from a per-nonzero end bitmask and closes the
- *                 fibers of a few steps together, 3 stages the gathered factor
- *                 rows in shared memory with bulk asynchronous copies (FP32
- *                 factors with R % 4 == 0 and R <= 32; other shapes use 2);
- *                 0 lets the library choose.  All compute the same sums in the
- *                 same order.
+ *                 fibers of a few steps together; 0 lets the library choose.
+ *                 Other values are refused (DFACTO_EINVAL).  Both compute the
+ *                 same sums in the same order.
  */
 typedef struct dfacto_options {
   int32_t rank;
@@ -142,7 +141,7 @@ const char* dfacto_status_str(dfacto_status s);
  *           of nonzero t.  Host or device.
  *   val     float[nnz], host or device.  Explicit zeros are kept as observed
  *           entries (the observed set of Sec. 2).
- *   nnz     0 <= nnz < 2^31.
+ *   nnz     0 <= nnz <= 2^31 - 2^16 (2,147,418,112).
  *   dims    host int32[3], each >= 1.
  *   opt     build options (rank, factor storage, ...); NULL means rank 1.
  *   stream  cudaStream_t the handle will use for all its work (NULL: the
@@ -261,11 +260,12 @@ dfacto_status dfacto_get_csr(dfacto_t* h, int mode, dfacto_csr_view* view);
  * Its scratch (segment starts and the partial sums of rows shared between
  * blocks) lives in one fixed 16 MiB device array inside the library.  Every
  * GPU that loads the library holds that array until the process exits.  The
- * problem must fit in it: about 250 million nonzeros at R = 32 (the layout is
- * 4 bytes per 128 nonzeros plus 8 * R + 8 bytes per 8,192 nonzeros at R = 32).
+ * problem must fit in it: about 260 million nonzeros at R = 32 (4 bytes per
+ * 128 nonzeros plus 8 * R + 8 bytes per 8,192 nonzeros when R is a multiple of
+ * 8) and about 310 million at R = 10 (the same per 4,096 nonzeros).
  *   csr     host struct of device pointers to the flattened CSR copy of mode n,
  *           in the layout dfacto_get_csr describes (from a handle, or built by
- *           the caller the same way); nnz < 2^31.
+ *           the caller the same way); nnz <= 2^31 - 2^16.
  *   F_in    device float[dims[(n+1) mod 3] x R], row-major: the factor indexed
  *           by nz_idx.
  *   F_f     device float[dims[(n+2) mod 3] x R], row-major: the factor indexed
@@ -279,11 +279,15 @@ dfacto_status dfacto_get_csr(dfacto_t* h, int mode, dfacto_csr_view* view);
  *
  * The first call on a device, with that device current, looks up the device
  * address of the array (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the one array and a call leaves its
- * contents behind: calls whose work may overlap on the GPU (different streams
- * or threads without ordering) race on it and must be serialised by the
- * caller.  Nothing in the array needs to start at zero: each call writes every
- * scratch value it later reads.
+ * stream capture.  Under CUDA's lazy module loading (the default) that first
+ * call, and the first call for each walk shape (R), may also load the
+ * library's device code and the array itself, which takes device memory: make
+ * one call per device and R before the section that must not allocate (its
+ * results can be discarded), or run with CUDA_MODULE_LOADING=EAGER.  All calls
+ * share the one array and a call leaves its contents behind: calls whose work
+ * may overlap on the GPU (different streams or threads without ordering) race
+ * on it and must be serialised by the caller.  Nothing in the array needs to
+ * start at zero: each call writes every scratch value it later reads.
  */
 dfacto_status dfacto_mttkrp_noalloc(const dfacto_csr_view* csr, const float* F_in, const float* F_f,
                                     int32_t R, float* out, void* stream);

@@ -10,10 +10,23 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "smem_optin.h"
 
 namespace dfacto {
 
 std::atomic<long long> g_launches{0};
+
+cudaError_t ensure_dynamic_smem(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static SmemOptIn optin;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  return static_cast<cudaError_t>(optin.ensure(kernel, dev, bytes, [&] {
+    return static_cast<int>(
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  }));
+}
 
 dfacto_status fail(dfacto_t* h, dfacto_status s, const std::string& what) {
   if (h) h->err = what;
@@ -134,7 +147,6 @@ dfacto_status read_back(dfacto_t* h) {
                              cudaMemcpyDeviceToHost, h->stream));
   DF_CUDA(h, cudaStreamSynchronize(h->stream));
   if (h->host_flags[kFlagInternal]) return fail(h, DFACTO_EINTERNAL, "internal consistency check failed");
-  if (h->host_flags[kFlagTimeout]) return fail(h, DFACTO_ETIMEOUT, "a device-side wait gave up");
   return DFACTO_OK;
 }
 
@@ -255,7 +267,7 @@ dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, co
                            const dfacto_options* opt_in, void* stream, dfacto_t** out) {
   if (!out) return DFACTO_EINVAL;
   *out = nullptr;
-  if (!dims || nnz < 0 || nnz >= (int64_t(1) << 31) || (nnz > 0 && (!idx || !val)))
+  if (!dims || nnz < 0 || nnz > kMaxNnz || (nnz > 0 && (!idx || !val)))
     return DFACTO_EINVAL;
   for (int m = 0; m < 3; ++m)
     if (dims[m] < 1) return DFACTO_EINVAL;
@@ -268,8 +280,8 @@ dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, co
   if (!(opt.lambda_reg >= 0.0)) return DFACTO_EINVAL;
   if (opt.vec != 0 && (opt.vec != 1 && opt.vec != 2 && opt.vec != 4 && opt.vec != 8)) return DFACTO_EINVAL;
   if (opt.vec != 0 && R % opt.vec != 0) return DFACTO_EINVAL;
-  if (opt.seg_nnz < 0) return DFACTO_EINVAL;
-  if (opt.walk < 0 || opt.walk > 3) return DFACTO_EINVAL;
+  if (opt.seg_nnz < 0 || opt.seg_nnz > kMaxSeg) return DFACTO_EINVAL;
+  if (opt.walk < 0 || opt.walk > 2) return DFACTO_EINVAL;
 
   dfacto_t* h = new (std::nothrow) dfacto_handle();
   if (!h) return DFACTO_ENOMEM;
@@ -356,16 +368,7 @@ dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, co
   }
   for (int m = 0; m < 3; ++m) {
     h->m[m].cfg = choose_walk(R, h->dtype, nnz, h->m[m].nfib, opt.seg_nnz, opt.vec);
-    if (opt.walk == 3) {
-      // staged walk: one 32-lane group per segment, lane c on column c
-      // (shapes it does not take keep the bitmask walk)
-      WalkCfg& c = h->m[m].cfg;
-      c.kernel = stage_supported(h->dtype, R) ? 3 : 2;
-      if (c.kernel == 3) {
-        c.vec = 1;
-        c.G = 32;
-      }
-    } else if (opt.walk > 0) {
+    if (opt.walk > 0) {
       h->m[m].cfg.kernel = opt.walk;
     }
   }

@@ -629,16 +629,16 @@ dfacto_status dfacto_batch_create(dfacto_t* const* jobs, int32_t n, const dfacto
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(DFACTO_ECUDA);
 
   // Rank classes: jobs with equal (R, factor type), in job order; a class is
-  // closed before its nonzeros or pool rows would reach 2^31.
-  const int64_t kLimit = (int64_t(1) << 31) - 1;
+  // closed before its nonzeros would pass kMaxNnz or its pool rows 2^31 - 1.
+  const int64_t kRowLimit = (int64_t(1) << 31) - 1;
   for (int j = 0; j < n; ++j) {
     const dfacto_t* h = b->jobs[j];
     int k = -1;
     for (int c = (int)b->cls.size() - 1; c >= 0; --c) {
       const BatchClass& C = b->cls[c];
       if (C.R != h->R || C.dtype != h->dtype) continue;
-      bool fits = C.nnz + h->nnz <= kLimit;
-      for (int m = 0; m < 3; ++m) fits = fits && C.rows[m] + h->dims[m] <= kLimit;
+      bool fits = C.nnz + h->nnz <= kMaxNnz;
+      for (int m = 0; m < 3; ++m) fits = fits && C.rows[m] + h->dims[m] <= kRowLimit;
       if (fits) k = c;
       break;
     }

@@ -6,12 +6,8 @@ namespace dfacto {
 template <typename T>
 cudaError_t launch_walk2_multi(const MultiWalkParams& mp, size_t smem, int grid, cudaStream_t s) {
   auto k = mttkrp_walk2_multi<T>;
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(k), smem);
+  if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
   k<<<(unsigned)grid, kWalkWarps * 32, smem, s>>>(mp);
   DF_COUNT();

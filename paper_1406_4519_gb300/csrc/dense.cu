@@ -1415,13 +1415,11 @@ __global__ void __launch_bounds__(kT, 2) gd_update_gram(T* __restrict__ F, const
   store_gram_partial<RT>(a32, reinterpret_cast<double*>(tF), R, gpart, blockIdx.x);
 }
 
-// Opt a kernel in to `bytes` of dynamic shared memory (above the default
-// 48 KB), once per kernel; later calls return the first call's result.
+// Opt a kernel in to `Bytes` of dynamic shared memory (above the default
+// 48 KB) on the current device (once per kernel and device).
 template <auto Kernel, size_t Bytes>
 cudaError_t opt_in_smem() {
-  static const cudaError_t e =
-      cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Bytes);
-  return e;
+  return ensure_dynamic_smem(reinterpret_cast<const void*>(Kernel), Bytes);
 }
 
 template <int RT>
@@ -1543,7 +1541,8 @@ namespace {
 // limit for large R.
 template <typename K>
 void allow_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // a failure shows up as the launch error that follows
+  ensure_dynamic_smem(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 size_t tile_bytes(int R, int copies) {

@@ -441,7 +441,6 @@ dfacto_status dual_pass(dfacto_t* h) {
   // The mode-1 walk's segments; dual_walk2 keeps five accumulators and two
   // gathered rows per lane, so its lanes take at most four columns.
   WalkCfg cfg = M.cfg;
-  if (cfg.kernel == 3) cfg.kernel = 2;  // same segments; the staged walk has no dual form
   if (cfg.kernel == 2 && cfg.vec > 4) {
     cfg.vec = 4;
     int G = 1;

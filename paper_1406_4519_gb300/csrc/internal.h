@@ -18,11 +18,17 @@ struct WalkCfg {
   int vec = 0;    // columns per lane (1, 2, 4, 8)
   int G = 0;      // lanes per group (power of two, G * vec >= R)
   int seg = 0;    // nonzeros per segment (multiple of 32)
-  int kernel = 1; // 1: mttkrp_walk, 2: mttkrp_walk2 (fiber ends from a bitmask),
-                  // 3: mttkrp_stage (rows staged in shared memory by bulk copies)
+  int kernel = 1; // 1: mttkrp_walk, 2: mttkrp_walk2 (fiber ends from a bitmask)
 };
 
 constexpr int kWalkWarps = 8;  // warps per MTTKRP CTA
+
+// Largest nonzero count of a tensor (and of a batch's rank class) and largest
+// MTTKRP segment: the walks keep nonzero positions in 32-bit integers, and a
+// segment end (position + segment length + one lane group) must stay below
+// 2^31.
+constexpr int64_t kMaxNnz = (int64_t(1) << 31) - (int64_t(1) << 16);
+constexpr int kMaxSeg = 4096;
 
 // Flattened CSR copy of one mode (Sec. 3): the nonzero rows of
 // (X^{n+1})^T ("fibers") and the fixed pattern of M^r.
@@ -64,7 +70,6 @@ enum Flag : int {
   kFlagSingular,      // a pseudo-inverse was used
   kFlagLsFail,        // line search failed
   kFlagInternal,      // internal check failed
-  kFlagTimeout,       // a bounded device-side wait gave up
   kNumFlags
 };
 
@@ -129,6 +134,12 @@ dfacto_status cuda_fail(dfacto_t* h, cudaError_t e, const char* what);
     if (e_ != cudaSuccess) return ::dfacto::cuda_fail((h), e_, #call); \
   } while (0)
 
+// ---- kernels with more than 48 KB of dynamic shared memory ---------------
+// Raise `kernel`'s dynamic shared memory limit to `bytes` on the current
+// device, once per (kernel, device, size) and thread-safe (the attribute is a
+// per-device setting).  No-op at or below the default 48 KB.
+cudaError_t ensure_dynamic_smem(const void* kernel, size_t bytes);
+
 // ---- memory ---------------------------------------------------------------
 dfacto_status dalloc(dfacto_t* h, void** p, size_t bytes);
 void dfree(dfacto_t* h, void* p, size_t bytes);
@@ -146,8 +157,6 @@ dfacto_status ensure_segments(dfacto_t* h, int mode);
 
 // ---- MTTKRP (mttkrp*.cu) --------------------------------------------------
 WalkCfg choose_walk(int R, int dtype, int64_t nnz, int64_t nfib, int seg_opt, int vec_opt);
-// Shapes the staged walk (kernel 3) takes: FP32 factors, R % 4 == 0, R <= 32.
-bool stage_supported(int dtype, int R);
 dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out);
 
 // ---- batches (batch.cu, dense.cu) -----------------------------------------

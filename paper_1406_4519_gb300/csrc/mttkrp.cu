@@ -16,6 +16,7 @@ constexpr int kAhead = 8;  // carry entries a warp loads before adding them
 // that starts inside c, add up r's partials from CTAs c .. c_last in CTA order
 // (eight warps take interleaved entries, then their sums are added in warp
 // order) and store N[r, :].  Then all blocks zero the rows without fibers.
+// `bad` (nullable) is set when a carry entry does not name the row it should.
 __global__ void __launch_bounds__(kFixThreads) mttkrp_fixup(
     const int32_t* __restrict__ carry_row, const float* __restrict__ carry,
     const int64_t* __restrict__ fiber_ptr, const int64_t* __restrict__ nz_ptr, float* __restrict__ out,
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(kFixThreads) mttkrp_fixup(
       }
       if (lane < kAhead) {
         const int64_t j = j0 + (int64_t)lane * kFixWarps;
-        if (j > 0 && j < ne && carry_row[2 * (c + j)] != r) atomicOr(bad, 1);
+        if (bad && j > 0 && j < ne && carry_row[2 * (c + j)] != r) atomicOr(bad, 1);
       }
     }
 #pragma unroll
@@ -174,9 +175,7 @@ dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out) {
   if (ncta > 0) {
     const size_t smem = sizeof(float) * (size_t)(2 * segs + 2 * kWalkWarps) * h->R;
     cudaError_t e;
-    if (cfg.kernel == 3)
-      e = launch_walk_stage(a, ncta, h->flags + kFlagTimeout, h->stream);
-    else if (cfg.kernel == 2)
+    if (cfg.kernel == 2)
       e = (h->dtype == DFACTO_BF16) ? launch_walk2<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, h->stream)
                                     : launch_walk2<float>(cfg.vec, cfg.G, a, ncta, h->stream);
     else

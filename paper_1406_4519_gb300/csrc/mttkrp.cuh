@@ -480,6 +480,8 @@ __device__ __forceinline__ void walk2_cta(const MttkrpParams& a, int cta, float*
   const int col0 = c * VEC;
   const bool colok = col0 < R;
   const int sl = warp * NG + g;
+  // Positions fit in int: nnz <= kMaxNnz and seg <= kMaxSeg keep p0 + seg + G
+  // below 2^31 (the bounds are formed in 64 bits first).
   const int nnz = (int)a.nnz;
   const int cta_p0 = (int)min((int64_t)cta * SEGS * a.seg, a.nnz);
   const int cta_p1 = (int)min((int64_t)cta_p0 + (int64_t)SEGS * a.seg, a.nnz);
@@ -712,11 +714,5 @@ cudaError_t launch_walk(int vec, int G, const MttkrpParams& a, int64_t ncta, siz
                         cudaStream_t s);
 template <typename T>
 cudaError_t launch_walk2(int vec, int G, const MttkrpParams& a, int64_t ncta, cudaStream_t s);
-
-// The staged walk (walk = 3, mttkrp_stage.cu): FP32 factors, R % 4 == 0,
-// R <= 32, one segment of a.seg (% 32 == 0) nonzeros per warp; a bounded wait
-// that gives up sets *timeout_flag.
-size_t stage_smem_bytes(int R);
-cudaError_t launch_walk_stage(const MttkrpParams& a, int64_t ncta, int32_t* timeout_flag, cudaStream_t s);
 
 }  // namespace dfacto

@@ -8,12 +8,8 @@ static cudaError_t go(const MttkrpParams& a, int64_t ncta, size_t smem, cudaStre
   auto k = mttkrp_walk<__nv_bfloat16, VEC, G>;
   // Opt in to the dynamic shared memory this launch needs (the default limit
   // is 48 KB including the kernel's static shared memory).
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(k), smem);
+  if (e != cudaSuccess) return e;
   k<<<(unsigned)ncta, kWalkWarps * 32, smem, s>>>(a);
   DF_COUNT();
   return cudaGetLastError();
@@ -36,12 +32,8 @@ template <int VEC, int G>
 static cudaError_t go2(const MttkrpParams& a, int64_t ncta, cudaStream_t s) {
   auto k = mttkrp_walk2<__nv_bfloat16, VEC, G>;
   const size_t smem = Walk2Shape<__nv_bfloat16, VEC, G>::smem_bytes(a.R);
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(k), smem);
+  if (e != cudaSuccess) return e;
   k<<<(unsigned)ncta, kWalkWarps * 32, smem, s>>>(a);
   DF_COUNT();
   return cudaGetLastError();

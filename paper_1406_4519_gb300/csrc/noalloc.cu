@@ -40,12 +40,8 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 template <int VEC, int G>
 cudaError_t go(const MttkrpParams& a, int64_t ncta, size_t smem, cudaStream_t s) {
   auto k = mttkrp_walk<float, VEC, G, true>;
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(k), smem);
+  if (e != cudaSuccess) return e;
   k<<<(unsigned)ncta, kWalkWarps * 32, smem, s>>>(a);
   DF_COUNT();
   return cudaGetLastError();
@@ -73,25 +69,25 @@ extern "C" dfacto_status dfacto_mttkrp_noalloc(const dfacto_csr_view* csr, const
                                                void* stream) {
   if (!csr || !out || R < 1 || R > 128 || (R > 32 && R % 4 != 0)) return DFACTO_EINVAL;
   const int64_t nnz = csr->nnz, nfib = csr->nfib, dim_o = csr->dim_o;
-  if (nnz < 0 || nnz >= (int64_t(1) << 31) || nfib < 0 || nfib > nnz || dim_o < 1 || !csr->fiber_ptr)
+  if (nnz < 0 || nnz > kMaxNnz || nfib < 0 || nfib > nnz || dim_o < 1 || !csr->fiber_ptr)
     return DFACTO_EINVAL;
   if (nnz > 0 && (!csr->fiber_idx || !csr->nz_ptr || !csr->nz_idx || !csr->nz_val || !F_in || !F_f))
     return DFACTO_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-  // Eight columns per lane where R allows it: 64 segments per block, which
-  // fixes the scratch per nonzero stated in the header.
+  // Eight columns per lane where R allows it (R a multiple of 8: R / 8 lanes
+  // per segment), fewer otherwise; the walk shape fixes the scratch per
+  // nonzero stated in the header.
   const WalkCfg cfg = choose_walk(R, DFACTO_F32, nnz, nfib, 0, 8);
   const int segs = kWalkWarps * (32 / cfg.G);
   const int64_t P = (int64_t)segs * cfg.seg;
   const int64_t ncta = (nnz + P - 1) / P;
   const int64_t nseg = (nnz + cfg.seg - 1) / cfg.seg;
 
-  // Scratch layout: seg_fib[nseg] | carry[ncta][2][R] | carry_row[ncta][2] | bad.
+  // Scratch layout: seg_fib[nseg] | carry[ncta][2][R] | carry_row[ncta][2].
   const size_t off_carry = align256(sizeof(int32_t) * (size_t)nseg);
   const size_t off_rows = off_carry + align256(sizeof(float) * 2 * (size_t)R * ncta);
-  const size_t off_bad = off_rows + align256(sizeof(int32_t) * 2 * (size_t)ncta);
-  const size_t need = off_bad + 256;
+  const size_t need = off_rows + align256(sizeof(int32_t) * 2 * (size_t)ncta);
   if (need > kNoAllocScratchBytes) return DFACTO_ENOMEM;
 
   unsigned char* scratch = nullptr;
@@ -102,7 +98,6 @@ extern "C" dfacto_status dfacto_mttkrp_noalloc(const dfacto_csr_view* csr, const
   int32_t* seg_fib = reinterpret_cast<int32_t*>(scratch);
   float* carry = reinterpret_cast<float*>(scratch + off_carry);
   int32_t* carry_row = reinterpret_cast<int32_t*>(scratch + off_rows);
-  int32_t* bad = reinterpret_cast<int32_t*>(scratch + off_bad);
 
   cudaError_t e = launch_segment_starts(csr->nz_ptr, nfib, nseg, cfg.seg, seg_fib, s);
   if (e == cudaSuccess && ncta > 0) {
@@ -129,7 +124,7 @@ extern "C" dfacto_status dfacto_mttkrp_noalloc(const dfacto_csr_view* csr, const
   }
   if (e == cudaSuccess)
     e = launch_mttkrp_fixup(carry_row, carry, csr->fiber_ptr, csr->nz_ptr, out, R, P, ncta, dim_o,
-                            bad, s);
+                            /*bad=*/nullptr, s);  // no status word to report it through
   if (e != cudaSuccess) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? DFACTO_ENOMEM : DFACTO_ECUDA;

@@ -32,6 +32,22 @@ import time
 from dataclasses import dataclass, field
 from typing import Callable, Dict, List, Optional, Sequence
 
+# Library statuses that concern one request only (include/dfacto.h): bad
+# arguments, a coordinate outside dims, a duplicate coordinate, no device
+# memory for this tensor.  Any other failure (ECUDA leaves the context unusable,
+# EINTERNAL is a library fault) stops the server.
+REQUEST_STATUSES = (1, 2, 3, 4)  # DFACTO_EINVAL, ERANGE, EDUP, ENOMEM
+
+
+def is_request_failure(e: BaseException) -> bool:
+    """True when building one request failed for a reason of its own (its
+    tensor or its size), so that the request can fail alone."""
+    status = getattr(e, "status", None)
+    if status is not None:
+        return status in REQUEST_STATUSES
+    # input that cannot describe a tensor, or no host/device memory for it
+    return isinstance(e, (ValueError, MemoryError)) or type(e).__name__ == "OutOfMemoryError"
+
 
 @dataclass
 class JobSpec:
@@ -249,7 +265,9 @@ def serve(jobs: Sequence[JobSpec], budget_bytes: float = 120e9, max_iters: int =
                 try:
                     engine.build(job)
                     built.append(job)
-                except Exception as e:  # a request that cannot be built fails alone
+                except Exception as e:
+                    if not is_request_failure(e):
+                        raise  # the device or the library is at fault: stop serving
                     sch.reject(job, clock() - t0, "%s: %s" % (type(e).__name__, e))
             if built:
                 sch.admit(built, clock() - t0)

@@ -95,7 +95,14 @@ def test_host_side_argument_checks(lib):
     opt = dfacto.dfacto_options_init(8, lambda_reg=-1.0)
     assert lib.dfacto_build(None, None, 0, dims, ctypes.byref(opt), None,
                             ctypes.byref(out)) == dfacto.EINVAL
-    for walk in (-1, 4):  # walks 0 (library's choice) to 3 exist
+    # nonzero positions stay 32-bit in the walks: at most 2^31 - 2^16 nonzeros
+    # (refused before the null pointers are looked at)
+    assert lib.dfacto_build(None, None, 2 ** 31 - 2 ** 16 + 1, dims, None, None,
+                            ctypes.byref(out)) == dfacto.EINVAL
+    opt = dfacto.dfacto_options_init(8, seg_nnz=4097)  # segments of at most 4096
+    assert lib.dfacto_build(None, None, 0, dims, ctypes.byref(opt), None,
+                            ctypes.byref(out)) == dfacto.EINVAL
+    for walk in (-1, 3, 4):  # walks 0 (library's choice), 1 and 2 exist
         opt = dfacto.dfacto_options_init(8, walk=walk)
         assert lib.dfacto_build(None, None, 0, dims, ctypes.byref(opt), None,
                                 ctypes.byref(out)) == dfacto.EINVAL

@@ -129,7 +129,7 @@ def test_mttkrp_appendix_d_exact():
     np.testing.assert_array_equal(t.mttkrp(0).cpu().numpy(), g["M"])
 
 
-@pytest.mark.parametrize("walk", [1, 2, 3])
+@pytest.mark.parametrize("walk", [1, 2])
 @pytest.mark.parametrize("R", [1, 3, 8, 10, 16, 32, 64])
 @pytest.mark.parametrize("seg", [32, 256])
 def test_mttkrp_uniform(R, seg, walk):
@@ -153,7 +153,7 @@ def test_mttkrp_lane_layouts(vec, walk):
         assert rel(host(t.mttkrp(mode)), oracle.mttkrp(ot, mode, Fh)) <= MTTKRP_TOL
 
 
-@pytest.mark.parametrize("walk", [1, 2, 3])
+@pytest.mark.parametrize("walk", [1, 2])
 @pytest.mark.parametrize("seg", [32, 128, 1024])
 def test_mttkrp_power_law_rows_span_many_ctas(seg, walk):
     """Zipf heads put ~10% of all nonzeros in one row and long fibers across
@@ -187,44 +187,6 @@ def test_preferential_attachment_csr_mttkrp_and_sweep(dims, nnz):
     for m in range(3):
         assert rel(after[m], Fo[m]) <= 1e-4, m
     assert abs(fit - fit_o) <= 1e-5
-
-
-@pytest.mark.parametrize("seg", [32, 128, 512])
-def test_staged_walk_equals_bitmask_walk_bitwise(seg):
-    """walk = 3 stages the gathered rows in shared memory; with one 32-lane
-    group per segment (R = 32, one column per lane) the bitmask walk has the
-    same segments and merge tree, so the sums are equal bit for bit."""
-    dims = [3000, 2000, 1000]
-    idx, val = synth.zipf_tensor(dims, 400000, [1.2, 1.1, 1.3], seed=31, device="cuda", values="cp")
-    F = synth.normal_factors(dims, 32, seed=32, device="cuda")
-    outs = []
-    for walk in (2, 3):
-        t = dfacto.Tensor(idx, val, dims, rank=32, seg_nnz=seg, vec=1, walk=walk)
-        t.set_factors(F)
-        outs.append([host(t.mttkrp(m)) for m in range(3)])
-    for m in range(3):
-        np.testing.assert_array_equal(outs[0][m], outs[1][m], err_msg="mode %d" % m)
-
-
-def test_staged_walk_als_and_gd_steps():
-    """A full ALS sweep and GD step with walk = 3 (its shapes and the dual
-    pass, which takes the bitmask walk's form) against the oracle."""
-    dims = [400, 300, 200]
-    idx, val = synth.zipf_tensor(dims, 60000, [1.2, 1.2, 1.2], seed=33, device="cuda", values="cp")
-    F = synth.normal_factors(dims, 16, seed=34, device="cuda")
-    t = dfacto.Tensor(idx, val, dims, rank=16, walk=3)
-    t.set_factors(F)
-    ot = as_oracle(idx, val, dims)
-    Fh = [host(f) for f in F]
-    st, fit = t.als_iter()
-    assert st == dfacto.OK
-    st_o, Fo, lam_o, fit_o = oracle.als_sweep(ot, Fh)
-    after = [host(f) for f in t.factors()]
-    for m in range(3):
-        assert rel(after[m], Fo[m]) <= 1e-4, m
-    assert abs(fit - fit_o) <= 1e-5
-    st, loss, alpha = t.gd_iter()
-    assert st in (dfacto.OK, dfacto.ELSFAIL) and np.isfinite(loss)
 
 
 def test_mttkrp_single_row_and_single_fiber():

@@ -157,17 +157,27 @@ def test_cap_applies_when_fit_keeps_moving():
     assert done[0].iters == 7
 
 
-class FailingEngine(FakeEngine):
-    """A FakeEngine whose build of the listed jobs raises (an unbuildable
-    request: out-of-range coordinates, duplicates, no memory)."""
+class StatusError(RuntimeError):
+    """Stands in for dfacto.DfactoError: an error carrying a library status."""
 
-    def __init__(self, clock, rates, bad):
+    def __init__(self, status):
+        super().__init__("status %d" % status)
+        self.status = status
+
+
+class FailingEngine(FakeEngine):
+    """A FakeEngine whose build of the listed jobs raises: an unbuildable
+    request (out-of-range coordinates, duplicates, no memory) by default, or
+    the given error."""
+
+    def __init__(self, clock, rates, bad, error=None):
         super().__init__(clock, rates)
         self.bad = set(bad)
+        self.error = error
 
     def build(self, job):
         if job.spec.job_id in self.bad:
-            raise RuntimeError("cannot build job %d" % job.spec.job_id)
+            raise self.error if self.error is not None else StatusError(2 + job.spec.job_id % 3)
         super().build(job)
 
 
@@ -186,6 +196,28 @@ def test_a_request_that_fails_to_build_fails_alone():
         assert by_id[jid].error is None and by_id[jid].iters == converge_sweep(0.5, 1e-4)
     s = serve.latency_stats(done)
     assert s["jobs"] == 3 and s["failed"] == 2
+
+
+@pytest.mark.parametrize("error", [StatusError(5), StatusError(9), RuntimeError("driver")])
+def test_a_device_or_library_failure_stops_the_server(error):
+    """ECUDA (the context is unusable), EINTERNAL and errors without a status
+    are not a request's own: the server re-raises them instead of serving on."""
+    clock = FakeClock()
+    eng = FailingEngine(clock, {i: 0.5 for i in range(3)}, bad=[1], error=error)
+    fp = serve.footprint_bytes([100, 100, 100], 1000, 8, 2)
+    with pytest.raises(type(error)):
+        serve.serve(specs(3, [0.0, 0.0, 0.001]), engine=eng, clock=clock, sleep=clock.sleep,
+                    max_iters=50, tol=1e-4, budget_bytes=2.5 * fp)
+
+
+def test_request_failure_classification():
+    for st in (1, 2, 3, 4):
+        assert serve.is_request_failure(StatusError(st))
+    for st in (5, 6, 7, 8, 9):
+        assert not serve.is_request_failure(StatusError(st))
+    assert serve.is_request_failure(ValueError("bad dims"))
+    assert serve.is_request_failure(MemoryError())
+    assert not serve.is_request_failure(RuntimeError("x"))
 
 
 def test_latency_stats():

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1406_4519_gb300 import dfacto, synth
 
 pytestmark = pytest.mark.gpu
@@ -38,8 +39,11 @@ def test_noalloc_matches_mttkrp_twice(kind, R):
     F = synth.normal_factors(dims, R, seed=7, device="cuda")
     t = dfacto.Tensor(idx, val, dims, rank=R)
     t.set_factors(F)
+    ot = oracle.Tensor(idx.cpu().numpy(), val.cpu().numpy(), dims)
+    Fh = [f.double().cpu().numpy() for f in F]
     for mode in range(3):
         want = t.mttkrp(mode)
+        exact = torch.from_numpy(oracle.mttkrp(ot, mode, Fh))  # FP64 definition
         csr = dfacto.dfacto_get_csr(t.h, mode)
         F_in, F_f = F[(mode + 1) % 3], F[(mode + 2) % 3]
         for call in range(2):  # the second call reuses the scratch the first left behind
@@ -48,6 +52,7 @@ def test_noalloc_matches_mttkrp_twice(kind, R):
             torch.cuda.synchronize()
             assert torch.isfinite(out).all()
             assert rel(out, want) <= TOL, (mode, call)
+            assert rel(out, exact) <= TOL, (mode, call)
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch():
