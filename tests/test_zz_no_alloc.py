@@ -57,16 +57,21 @@ def test_noalloc_matches_mttkrp_twice(kind, R):
 
 def test_noalloc_rejects_problems_beyond_its_scratch():
     """The size check happens on the host before any launch: a view claiming
-    2^31 - 1 nonzeros needs far more than 16 MiB and is refused."""
+    the largest accepted nonzero count (2^31 - 2^16) needs far more than
+    16 MiB and is refused with ENOMEM; one nonzero more is not a valid view."""
     dims = [50, 40, 30]
     idx, val = synth.uniform_tensor(dims, 2000, seed=3, device="cuda")
     t = dfacto.Tensor(idx, val, dims, rank=8)
     csr = dfacto.dfacto_get_csr(t.h, 0)
     big = dfacto.dfacto_csr_view()
     ctypes.pointer(big)[0] = csr
-    big.nnz = 2 ** 31 - 1
+    big.nnz = 2 ** 31 - 2 ** 16
     F = synth.normal_factors(dims, 8, seed=1, device="cuda")
     out = torch.zeros(dims[0], 8, device="cuda")
     with pytest.raises(dfacto.DfactoError) as e:
         dfacto.dfacto_mttkrp_noalloc(big, F[1], F[2], 8, out)
     assert e.value.status == dfacto.ENOMEM
+    big.nnz = 2 ** 31 - 2 ** 16 + 1
+    with pytest.raises(dfacto.DfactoError) as e:
+        dfacto.dfacto_mttkrp_noalloc(big, F[1], F[2], 8, out)
+    assert e.value.status == dfacto.EINVAL
