@@ -90,9 +90,10 @@ SERVE_WORKLOADS = {
                       n_req=2000, rate=50.0, seed=14064524, budget=120e9, cmp_req=500,
                       burst_req=500),
 }
-CPU_PHI = 0.1              # cpu_baseline: replica scaled by this factor (~10-30 s)
-REF_BUDGET_S = 120.0       # reference arm: target wall time of all W + K steps
-ORACLE_FULL_S_GUESS = 50.0  # rough oracle seconds per full-size sweep, sizes the replica
+# CPU legs (cpu_baseline, reference arm): the oracle runs the whole workload
+# when it has at most this many nonzeros (host copy ~1 GB at 50M); larger ones
+# (the 1.2B-nonzero workload) use a replica scaled to this count, which is said.
+ORACLE_FULL_NNZ = 60_000_000
 
 
 def parse_args():
@@ -120,8 +121,13 @@ def parse_args():
                          "prints the mean sweep time, no contract line")
     ap.add_argument("--phi", type=float, default=1.0)
     ap.add_argument("--oracle-sweep-npz", default=None,
-                    help="internal: time one oracle ALS sweep of the replica in this .npz file "
-                         "and print the seconds (run with the multi-core oracle build)")
+                    help="internal: time --oracle-reps oracle ALS sweeps of the tensor in this "
+                         ".npz file and print the seconds of each (run with the multi-core "
+                         "oracle build)")
+    ap.add_argument("--oracle-reps", type=int, default=1)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads reported beside the headline line "
+                         "(1.2B-nonzero tensor, batch, serving)")
     return ap.parse_args()
 
 
@@ -234,6 +240,23 @@ def make_replica(wl, phi, device):
     return dims, idx.cpu().numpy(), val.cpu().numpy(), F0
 
 
+def oracle_workload(wl, device):
+    """The workload as the CPU oracle takes it: the whole tensor when it has at
+    most ORACLE_FULL_NNZ nonzeros, else a replica scaled to that count (same
+    distributions and R).  Returns (phi, dims, idx, val, F0) on the host;
+    phi = 1 means the whole workload."""
+    phi = 1.0 if wl["nnz"] <= ORACLE_FULL_NNZ else ORACLE_FULL_NNZ / wl["nnz"]
+    dims, idx_np, val_np, F0 = make_replica(wl, phi, device)
+    return phi, dims, idx_np, val_np, F0
+
+
+def oracle_sample_text(phi, dims, nnz):
+    if phi == 1.0:
+        return "the whole workload (dims %s, %d nonzeros)" % (dims, nnz)
+    return ("the workload scaled by phi = %.4g (dims %s, %d nonzeros, same distributions and R; "
+            "the whole tensor does not fit the host-side budget), time / phi" % (phi, dims, nnz))
+
+
 def oracle_sweep_seconds(dims, idx_np, val_np, F0):
     """Wall time of one FP64 oracle ALS sweep (three factor updates + fit)."""
     import oracle
@@ -243,10 +266,10 @@ def oracle_sweep_seconds(dims, idx_np, val_np, F0):
     return time.perf_counter() - t0
 
 
-def oracle_sweep_seconds_all_cores(dims, idx_np, val_np, F0):
-    """One FP64 oracle ALS sweep with the OpenMP build of the same oracle source
-    on every host core (in a child process that loads that build).  Returns
-    (seconds, threads)."""
+def oracle_sweeps_all_cores(dims, idx_np, val_np, F0, reps=1):
+    """`reps` FP64 oracle ALS sweeps with the OpenMP build of the same oracle
+    source on every host core (in a child process that loads that build; it is
+    started with exec, not a bare fork).  Returns ([seconds per sweep], threads)."""
     import tempfile
 
     import numpy as np
@@ -255,20 +278,24 @@ def oracle_sweep_seconds_all_cores(dims, idx_np, val_np, F0):
     lib = oracle.build(openmp=True)
     threads = os.cpu_count() or 1
     with tempfile.TemporaryDirectory() as tmp:
-        path = os.path.join(tmp, "replica.npz")
+        path = os.path.join(tmp, "tensor.npz")
         np.savez(path, dims=np.asarray(dims), idx=idx_np, val=val_np, F0a=F0[0], F0b=F0[1],
                  F0c=F0[2])
         env = dict(os.environ, DFACTO_ORACLE_LIB=lib, OMP_NUM_THREADS=str(threads))
-        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sweep-npz", path],
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sweep-npz", path,
+                              "--oracle-reps", str(reps)],
                              capture_output=True, text=True, env=env, check=True).stdout
-    return float(out.strip().splitlines()[-1]), threads
+    secs = [float(x) for x in out.strip().splitlines()[-reps:]]
+    return secs, threads
 
 
-def run_oracle_sweep_npz(path):
+def run_oracle_sweep_npz(path, reps):
     import numpy as np
     d = np.load(path)
     F0 = [d["F0a"], d["F0b"], d["F0c"]]
-    print(oracle_sweep_seconds([int(x) for x in d["dims"]], d["idx"], d["val"], F0), flush=True)
+    dims, idx, val = [int(x) for x in d["dims"]], d["idx"], d["val"]
+    for _ in range(reps):
+        print(oracle_sweep_seconds(dims, idx, val, F0), flush=True)
 
 
 def emit(obj):
@@ -291,29 +318,27 @@ def max_over_ranks_of(x: float, world: int, device) -> float:
 
 
 def run_reference(args, rank, world):
+    """The FP64 oracle as it stands (its OpenMP build on every host core), one
+    ALS sweep of the workload per step, W + K steps; rank 0 only."""
     if rank != 0:
         return
+    import torch
     wl = WORKLOADS[args.workload]
-    n_steps = args.steps + args.warmup
-    phi = min(CPU_PHI, max(1.0 / 400, REF_BUDGET_S / (n_steps * ORACLE_FULL_S_GUESS)))
-    if wl["nnz"] * phi < 1000:
-        phi = 1.0 if wl["nnz"] <= 100_000 else phi
-    dims, idx_np, val_np, F0 = make_replica(wl, phi, "cpu")
-    for _ in range(args.warmup):
-        oracle_sweep_seconds(dims, idx_np, val_np, F0)
-    total = 0.0
-    for _ in range(args.steps):
-        total += oracle_sweep_seconds(dims, idx_np, val_np, F0) / phi
+    device = "cuda" if torch.cuda.is_available() else "cpu"  # input synthesis only
+    phi, dims, idx_np, val_np, F0 = oracle_workload(wl, device)
+    secs, threads = oracle_sweeps_all_cores(dims, idx_np, val_np, F0, args.warmup + args.steps)
+    timed = [x / phi for x in secs[args.warmup:]]
+    total = sum(timed)
     value = args.steps / total
-    sample = ("one FP64 ALS sweep per step on the workload scaled by phi = %.4g (dims %s, %d "
-              "nnz, same distributions and R), time / phi" % (phi, dims, val_np.shape[0]))
+    sample = ("one FP64 ALS sweep per step (the oracle source built with OpenMP, %d host "
+              "threads) on %s" % (threads, oracle_sample_text(phi, dims, val_np.shape[0])))
     emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s",
           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
           "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
           "config": {"workload": wl["desc"], "dims": wl["dims"], "nnz": wl["nnz"], "rank": wl["R"]},
-          "cpu_baseline": {"value": value, "unit": "iter/s", "cores": 1, "kind": "oracle",
-                           "sample": sample},
+          "cpu_baseline": {"value": value, "unit": "iter/s", "cores": threads, "kind": "oracle",
+                           "sample": sample, "whole_workload": phi == 1.0},
           "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0,
                   "d2h_bytes_per_step": 0}})
 
@@ -334,6 +359,106 @@ def algorithmic_bytes(info, uniq, dims, R, elem):
              + elem * R * (uniq[i_] + uniq[f]) + 4 * R * dims[o])
         out.append(b)
     return out
+
+
+def measure_large(wl, dev, dtypes=("f32", "bf16"), steps=3, warmup=1):
+    """ALS and GD iteration rates and the per-mode MTTKRP (time, algorithmic
+    GB/s, fraction of the measured HBM peak) of one single-tensor workload with
+    each factor storage type, inputs generated on the device and resident."""
+    import torch
+
+    from paper_1406_4519_gb300 import dfacto, synth
+    dims, R = wl["dims"], wl["R"]
+    t0 = time.perf_counter()
+    idx, val = make_tensor(wl, dims, wl["nnz"], dev)
+    F0 = synth.normal_factors(dims, R, seed=wl["seed"] + 1, device=dev)
+    uniq = [int(torch.unique(idx[m]).numel()) for m in range(3)]
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    peak, peak_kind = measured_peaks()
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn, n):
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    out = {"workload": wl["desc"], "dims": dims, "nnz": wl["nnz"], "rank": R,
+           "generate_s": gen_s, "steps": steps, "warmup": warmup,
+           "l2": "no flush: inputs exceed the 129 MB L2"}
+    for name in dtypes:
+        dtype = dfacto.BF16 if name == "bf16" else dfacto.F32
+        elem = 2 if name == "bf16" else 4
+        t1 = time.perf_counter()
+        t = dfacto.Tensor(idx, val, dims, rank=R, factor_dtype=dtype, stream=stream)
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t1
+        info = t.info()
+        t.set_factors(F0)
+        for _ in range(warmup):
+            t.als_iter(want_fit=False)
+        als_ms = timed(lambda: t.als_iter(want_fit=False), steps)
+        st, fit = t.als_iter(want_fit=True)
+        o = torch.empty(max(dims), R, dtype=torch.float32, device=dev)
+        mode_ms = []
+        for mode in range(3):
+            om = o[:dims[mode]]
+            t.mttkrp(mode, om)
+            mode_ms.append(timed(lambda: t.mttkrp(mode, om), steps))
+        del o
+        t.set_factors(F0)
+        st0, loss0, _ = t.gd_iter(want=True)
+        for _ in range(max(0, warmup - 1)):
+            t.gd_iter(want=False)
+        gd_ms = timed(lambda: t.gd_iter(want=False), steps)
+        st1, loss1, alpha = t.gd_iter(want=True)
+        alg = algorithmic_bytes(info, uniq, dims, R, elem)
+        gbs = [b / (m * 1e-3) / 1e9 for b, m in zip(alg, mode_ms)]
+        out[name] = {"build_s": build_s, "nfib": list(info.nfib),
+                     "als_iter_per_s": 1e3 / als_ms, "als_ms": als_ms, "als_fit": fit,
+                     "gd_iter_per_s": 1e3 / gd_ms, "gd_ms": gd_ms, "gd_alpha": alpha,
+                     "gd_loss_first_step": loss0, "gd_loss_last_step": loss1,
+                     "mttkrp_ms_per_mode": mode_ms, "algorithmic_bytes_per_mode": alg,
+                     "mttkrp_gbs_per_mode": gbs,
+                     "mttkrp_frac_per_mode": [g / peak for g in gbs],
+                     "mttkrp_frac": sum(alg) / (sum(mode_ms) * 1e-3) / 1e9 / peak,
+                     "peak": peak, "peak_kind": peak_kind}
+        del t
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    del idx, val, F0
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_extras(dev):
+    """The other workloads of the measurement plan, reported beside the headline
+    line: the 1.2B-nonzero tensor (FP32 and BF16 factors), the 256-job batch and
+    the 2,000-request serving run.  A workload that fails is reported with its
+    error instead of stopping the run."""
+    from paper_1406_4519_gb300 import dfacto
+    ex = {}
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    for key, fn in (("zipf1200M", lambda: measure_large(WORKLOADS["zipf1200M"], dev)),
+                    ("batch256", lambda: measure_batch(BATCH_WORKLOADS["batch256"], dfacto.F32, 10,
+                                                       3, dev)),
+                    ("serve2000", lambda: measure_serve(SERVE_WORKLOADS["serve2000"], dev))):
+        t0 = time.perf_counter()
+        try:
+            ex[key] = fn()
+        except Exception as e:  # reported, not fatal to the headline line
+            ex[key] = {"error": "%s: %s" % (type(e).__name__, str(e)[:300])}
+        ex[key]["wall_s"] = time.perf_counter() - t0
+    clocks.stop()
+    ex["clocks"] = clocks.summary()
+    return ex
 
 
 def run_ours(args, rank, world, local_rank):
@@ -486,22 +611,33 @@ def run_ours(args, rank, world, local_rank):
                "what": "per step: dfacto_build from pinned host COO, set_factors from host, one "
                        "ALS sweep with fit read-back, get_factors to pinned host"}
 
-    # -- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ------------
+    # -- CPU baseline: the oracle on the host cores (rank 0, N = 1) ---------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        phi = 1.0 if wl["nnz"] <= 100_000 else CPU_PHI
-        rdims, idx_np, val_np, F0_np = make_replica(wl, phi, dev)
-        t_s = oracle_sweep_seconds(rdims, idx_np, val_np, F0_np)
-        sample = ("one FP64 ALS sweep on the workload scaled by phi = %g (dims %s, %d nnz, same "
-                  "distributions and R), time / phi" % (phi, rdims, val_np.shape[0]))
+        phi, rdims, idx_np, val_np, F0_np = oracle_workload(wl, dev)
+        t_s = oracle_sweep_seconds(rdims, idx_np, val_np, F0_np) / phi
+        text = oracle_sample_text(phi, rdims, val_np.shape[0])
         try:
-            t_m, threads = oracle_sweep_seconds_all_cores(rdims, idx_np, val_np, F0_np)
-            sample += "; the oracle source built with OpenMP on every host core: %.2f s" % t_m
+            secs, threads = oracle_sweeps_all_cores(rdims, idx_np, val_np, F0_np, 1)
+            t_m = secs[0] / phi
+            sample = ("one FP64 ALS sweep (the oracle source built with OpenMP, %d host threads: "
+                      "%.2f s) on %s" % (threads, t_m, text))
         except Exception as e:  # no OpenMP toolchain: the single-threaded figure only
             t_m, threads = t_s, 1
-            sample += "; single-threaded (multi-core build unavailable: %s)" % str(e)[:120]
-        cpu = {"value": phi / t_m, "unit": "iter/s", "cores": threads, "kind": "oracle",
-               "sample": sample, "single_thread": {"value": phi / t_s, "cores": 1, "seconds": t_s}}
+            sample = ("one FP64 ALS sweep, single-threaded (multi-core build unavailable: %s) on %s"
+                      % (str(e)[:120], text))
+        cpu = {"value": 1.0 / t_m, "unit": "iter/s", "cores": threads, "kind": "oracle",
+               "sample": sample, "whole_workload": phi == 1.0,
+               "single_thread": {"value": 1.0 / t_s, "cores": 1, "seconds": t_s}}
+        del idx_np, val_np, F0_np
+
+    # -- the other workloads, reported beside the headline (rank 0, N = 1) --------
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == "zipf50M":
+        del idx, val
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        extras = measure_extras(dev)
 
     if rank != 0:
         return
@@ -530,7 +666,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks,
         "gd_iter_per_s": 1e3 / gd_ms, "gd_ms": gd_ms, "gd_alpha": alpha, "gd_loss": loss,
-        "als_fit": fit, "build_s": build_s,
+        "als_fit": fit, "build_s": build_s, "extras": extras,
     })
 
 
@@ -555,24 +691,20 @@ def make_batch_jobs(wl, dtype, dev):
     return specs, jobs, alg
 
 
-def run_batch(args, rank, world, local_rank):
-    """One step = one ALS sweep of every job of the batch (graph replay), inputs
-    resident; value = job-sweeps per second.  Also timed: the same sweeps issued
-    job by job through the single-tensor entry point."""
+def measure_batch(wl, dtype, steps, warmup, dev, autotune=True):
+    """One ALS sweep of every job of the batch (graph replay) per step, inputs
+    resident; also the same sweeps issued job by job through the single-tensor
+    entry point.  Returns a dict of the measurements."""
     import torch
 
     from paper_1406_4519_gb300 import dfacto
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    wl = BATCH_WORKLOADS[args.workload]
-    dtype = dfacto.BF16 if args.dtype == "bf16" else dfacto.F32
     specs, jobs, alg = make_batch_jobs(wl, dtype, dev)
     n = len(jobs)
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     # -- job by job (plain per-job ALS) ------------------------------------------
-    seq_steps = max(1, min(args.steps, 3))
+    seq_steps = max(1, min(steps, 3))
     for t in jobs:
         t.als_iter(want_fit=False)
     torch.cuda.synchronize()
@@ -587,64 +719,103 @@ def run_batch(args, rank, world, local_rank):
 
     # -- the batch -------------------------------------------------------------------
     t0 = time.perf_counter()
-    b = dfacto.Batch(jobs, stream=stream)
+    b = dfacto.Batch(jobs, stream=stream, autotune=autotune)
     create_s = time.perf_counter() - t0
-    for _ in range(max(args.warmup, 3)):  # first sweep eager, second captures the graph
+    for _ in range(max(warmup, 3)):  # first sweep eager, second captures the graph
         b.als_iter(want_fits=False)
     torch.cuda.synchronize()
-    sampler = ClockSampler(local_rank)
+    sampler = ClockSampler(dev.index or 0)
     sampler.start()
     launches0 = dfacto.dfacto_launch_count()
     e0, e1 = ev(), ev()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         b.als_iter(want_fits=False)
     e1.record(stream)
     torch.cuda.synchronize()
     sampler.stop()
     launches = dfacto.dfacto_launch_count() - launches0
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     st, fits = b.als_iter(want_fits=True)
     classes = [dict(rank=c.rank, dtype="bf16" if c.factor_dtype == dfacto.BF16 else "f32",
                     jobs=c.n_jobs, nnz=c.nnz, vec=c.vec, lanes=c.lanes, seg_nnz=c.seg_nnz,
                     tuned_mttkrp_ms=c.tuned_ms) for c in b.classes()]
     b.close()
+    del jobs
+    torch.cuda.synchronize()
     peak, peak_kind = measured_peaks()
     total_nnz = sum(sp["nnz"] for sp in specs)
+    return {"jobs": n, "total_nnz": total_nnz, "ms_per_sweep": ms,
+            "job_sweeps_per_s": n * 1e3 / ms, "job_by_job_ms_per_sweep": seq_ms,
+            "speedup_vs_job_by_job": seq_ms / ms, "create_s": create_s, "classes": classes,
+            "gpu_launches": launches, "clocks": sampler.summary(), "fit_mean": sum(fits) / n,
+            "alg_bytes": alg, "alg_gbs": alg / (ms * 1e-3) / 1e9, "peak": peak,
+            "peak_kind": peak_kind, "steps": steps, "warmup": max(warmup, 3)}
+
+
+def run_batch(args, rank, world, local_rank):
+    """One step = one ALS sweep of every job of the batch (graph replay), inputs
+    resident; value = job-sweeps per second.  Also timed: the same sweeps issued
+    job by job through the single-tensor entry point."""
+    import torch
+
+    from paper_1406_4519_gb300 import dfacto
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = BATCH_WORKLOADS[args.workload]
+    dtype = dfacto.BF16 if args.dtype == "bf16" else dfacto.F32
+    m = measure_batch(wl, dtype, args.steps, args.warmup, dev)
     if rank != 0:
         return
+    ms = m["ms_per_sweep"]
     emit({
-        "metric": "job-sweeps/s", "value": world * n * 1e3 / ms, "unit": "job-sweeps/s",
-        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+        "metric": "job-sweeps/s", "value": world * m["job_sweeps_per_s"], "unit": "job-sweeps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": m["warmup"], "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if dtype == dfacto.F32 else "bf16-storage/f32", "data": "synthetic",
-        "config": {"workload": wl["desc"], "jobs": n, "total_nnz": total_nnz,
+        "config": {"workload": wl["desc"], "jobs": m["jobs"], "total_nnz": m["total_nnz"],
                    "l2": "no flush: inputs (CSR of %.0fM nonzeros) exceed the 129 MB L2" %
-                         (total_nnz / 1e6),
+                         (m["total_nnz"] / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak,
-                     "unit": "GB/s", "frac": alg / (ms * 1e-3) / 1e9 / peak, "traffic": None,
+        "roofline": {"bound": "hbm", "achieved": m["alg_gbs"], "peak": m["peak"],
+                     "unit": "GB/s", "frac": m["alg_gbs"] / m["peak"], "traffic": None,
                      "kernel": "whole sweep: algorithmic MTTKRP bytes of every job and mode / "
-                               "sweep time", "peak_kind": peak_kind},
-        "job_by_job_ms_per_sweep": seq_ms, "speedup_vs_job_by_job": seq_ms / ms,
-        "create_s": create_s, "classes": classes, "gpu_launches": launches,
-        "clocks": sampler.summary(), "fit_mean": sum(fits) / n,
+                               "sweep time", "peak_kind": m["peak_kind"]},
+        "job_by_job_ms_per_sweep": m["job_by_job_ms_per_sweep"],
+        "speedup_vs_job_by_job": m["speedup_vs_job_by_job"],
+        "create_s": m["create_s"], "classes": m["classes"], "gpu_launches": m["gpu_launches"],
+        "clocks": m["clocks"], "fit_mean": m["fit_mean"],
     })
 
 
-def run_serve(args, rank, world, local_rank):
+def fit_agreement(done_a, done_b):
+    """Per request served by both servers: the relative difference of the final
+    fits and the difference of the sweeps run (a minus b)."""
+    fb = {j.spec.job_id: j for j in done_b if j.error is None and j.fits}
+    rel, dsw = [], []
+    for j in done_a:
+        k = fb.get(j.spec.job_id)
+        if j.error is not None or not j.fits or k is None:
+            continue
+        rel.append(abs(j.fits[-1] - k.fits[-1]) / max(abs(k.fits[-1]), 1e-300))
+        dsw.append(j.iters - k.iters)
+    if not rel:
+        return None
+    rel.sort()
+    return {"requests": len(rel), "final_fit_rel_diff_median": rel[len(rel) // 2],
+            "final_fit_rel_diff_max": rel[-1], "sweeps_diff_mean": sum(dsw) / len(dsw)}
+
+
+def measure_serve(wl, dev):
     """Requests arrive on a Poisson clock; the server admits, batches and
-    retires them in real time.  value = finished jobs per second over all
-    requests, with the p50 / p99 latency from arrival to factors on the host.
-    Beside it, on the first cmp_req arrivals, the same server and a server that
-    runs one job at a time with FP32 ALS (jobs/s, latency, final fit), and both
-    servers on a burst of burst_req requests arriving at once."""
+    retires them in real time.  Returns jobs/s over all requests with the
+    p50 / p99 latency from arrival to factors on the host; beside it, on the
+    first cmp_req arrivals, the same server and a server that runs one job at a
+    time with FP32 ALS (jobs/s, latency, final fit, per-request fit agreement),
+    and both servers on a burst of burst_req requests arriving at once."""
     import torch
 
     from paper_1406_4519_gb300 import dfacto, serve, synth
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    wl = SERVE_WORKLOADS[args.workload]
     specs = synth.batch_job_specs(wl["n_req"], wl["seed"])
     arrivals = synth.poisson_arrivals(wl["n_req"], wl["rate"], wl["seed"] + 1)
     # Inputs generated before the clock starts (as if received into device
@@ -661,26 +832,49 @@ def run_serve(args, rank, world, local_rank):
                               specs[i]["R"], make=(lambda i=i: data[i])) for i in range(n)]
 
     def batched(jobs):
-        return serve.latency_stats(serve.serve(jobs, budget_bytes=wl["budget"], max_iters=50,
-                                               tol=1e-4, factor_dtype=dfacto.BF16))
+        return serve.serve(jobs, budget_bytes=wl["budget"], max_iters=50, tol=1e-4,
+                           factor_dtype=dfacto.BF16)
 
     def sequential(jobs):
-        return serve.latency_stats(serve.serve_sequential(jobs, max_iters=50, tol=1e-4,
-                                                          factor_dtype=dfacto.F32))
+        return serve.serve_sequential(jobs, max_iters=50, tol=1e-4, factor_dtype=dfacto.F32)
 
     launches0 = dfacto.dfacto_launch_count()
-    sampler = ClockSampler(local_rank)
+    sampler = ClockSampler(dev.index or 0)
     sampler.start()
-    st = batched(jobs_of(wl["n_req"]))
+    st = serve.latency_stats(batched(jobs_of(wl["n_req"])))
     sampler.stop()
     launches = dfacto.dfacto_launch_count() - launches0
     nc = min(wl["cmp_req"], wl["n_req"])
-    cmp_b, cmp_s = batched(jobs_of(nc)), sequential(jobs_of(nc))
+    d_b, d_s = batched(jobs_of(nc)), sequential(jobs_of(nc))
+    cmp_b, cmp_s = serve.latency_stats(d_b), serve.latency_stats(d_s)
     nbu = min(wl["burst_req"], wl["n_req"])
-    bur_b, bur_s = batched(jobs_of(nbu, burst=True)), sequential(jobs_of(nbu, burst=True))
+    bur_b = serve.latency_stats(batched(jobs_of(nbu, burst=True)))
+    bur_s = serve.latency_stats(sequential(jobs_of(nbu, burst=True)))
+    del data
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    keep = ("jobs_per_s", "p50_s", "p99_s", "mean_s", "mean_iters", "mean_final_fit")
+    return {"requests": wl["n_req"], "jobs_per_s": st["jobs_per_s"], "all": st,
+            "latency": {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
+                        "mean_sweeps": st["mean_iters"], "mean_final_fit": st["mean_final_fit"]},
+            "same_requests": {"requests": nc, "batched_bf16": {k: cmp_b[k] for k in keep},
+                              "sequential_fp32": {k: cmp_s[k] for k in keep},
+                              "fit_agreement": fit_agreement(d_b, d_s)},
+            "burst": {"requests": nbu, "batched_bf16": {k: bur_b[k] for k in keep},
+                      "sequential_fp32": {k: bur_s[k] for k in keep}},
+            "gpu_launches": launches, "clocks": sampler.summary()}
+
+
+def run_serve(args, rank, world, local_rank):
+    """value = finished jobs per second of the serving loop (measure_serve)."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = SERVE_WORKLOADS[args.workload]
+    m = measure_serve(wl, dev)
     if rank != 0:
         return
-    keep = ("jobs_per_s", "p50_s", "p99_s", "mean_s", "mean_iters", "mean_final_fit")
+    st = m["all"]
     emit({
         "metric": "jobs/s", "value": world * st["jobs_per_s"], "unit": "jobs/s", "n_gpus": world,
         "steps": st["jobs"], "warmup": 0, "ms_per_step": 1e3 / st["jobs_per_s"],
@@ -690,13 +884,8 @@ def run_serve(args, rank, world, local_rank):
                    "l2": "no flush: every job's CSR is device-resident and the active set "
                          "exceeds the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "latency": {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
-                    "mean_sweeps": st["mean_iters"], "mean_final_fit": st["mean_final_fit"]},
-        "same_requests": {"requests": nc, "batched_bf16": {k: cmp_b[k] for k in keep},
-                          "sequential_fp32": {k: cmp_s[k] for k in keep}},
-        "burst": {"requests": nbu, "batched_bf16": {k: bur_b[k] for k in keep},
-                  "sequential_fp32": {k: bur_s[k] for k in keep}},
-        "gpu_launches": launches, "clocks": sampler.summary(),
+        "latency": m["latency"], "same_requests": m["same_requests"], "burst": m["burst"],
+        "gpu_launches": m["gpu_launches"], "clocks": m["clocks"],
     })
 
 
@@ -803,7 +992,7 @@ def run_mttkrp_only(args):
 def main():
     args = parse_args()
     if args.oracle_sweep_npz:
-        run_oracle_sweep_npz(args.oracle_sweep_npz)
+        run_oracle_sweep_npz(args.oracle_sweep_npz, args.oracle_reps)
         return
     if args.mttkrp_only:
         run_mttkrp_only(args)

@@ -11,7 +11,7 @@ check is one the oracle computes exactly at any size:
   * the cross-mode invariant sum_{o,r} N_n[o,r] F_n[o,r] = <X, [[A,B,C]]> for
     every mode n (all rows), against the oracle's FP64 inner product, within
     the bound 1e-5 ||N_n|| ||F_n|| that the normwise bar implies;
-  * BF16 factors (the 1.2B-nonzero workload, run with DFACTO_FULLSIZE_1200M=1):
+  * BF16 factors (the 1.2B-nonzero workload):
     within 1e-5 of the oracle fed the BF16-rounded factors and within 1e-2 of
     the oracle fed the FP32 ones;
   * one full ALS sweep of the 50M-nonzero workload against the oracle's sweep
@@ -19,7 +19,6 @@ check is one the oracle computes exactly at any size:
     FP32 bound).
 """
 import gc
-import os
 
 import numpy as np
 import pytest
@@ -110,10 +109,11 @@ def test_zipf50m_mttkrp_sampled_rows_invariant_and_als_sweep():
     torch.cuda.empty_cache()
 
 
-@pytest.mark.skipif(os.environ.get("DFACTO_FULLSIZE_1200M") != "1",
-                    reason="about six minutes (1.2B-nonzero generation, 19 GB of host copies, "
-                           "eight FP64 oracle passes); set DFACTO_FULLSIZE_1200M=1 to run")
 def test_zipf1200m_mttkrp_fp32_and_bf16_sampled_rows_and_invariant():
+    """The 1.2B-nonzero workload (66-bit (o, f, in) keys: the two-run chained
+    build) in the launch configuration bench.py times, FP32 and BF16 factors.
+    Several minutes: 1.2B-nonzero generation, 19 GB of host copies and the
+    oracle's FP64 passes over every nonzero."""
     wl, dims, idx, val, F = generate("zipf1200M")
     idx_h = idx.cpu().numpy()
     val_h = val.cpu().numpy()

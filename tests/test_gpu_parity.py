@@ -327,8 +327,10 @@ def fit_tolerance(ot, Fh, lam, eps=1e-6):
 
 
 def test_als_singular_gamma_reports_and_matches_pinv():
-    """Duplicated factor columns make Gamma singular: status ESINGULAR, and the
-    update matches the oracle's pseudo-inverse solution."""
+    """Duplicated factor columns make every Gamma of the sweep exactly singular
+    (Eq. kr-pseudo): the status is ESINGULAR, and the factors, lambda and fit
+    after the sweep equal the oracle's sweep, which takes the pseudo-inverse
+    (minimum-norm) solution of each mode in FP64."""
     dims = [30, 20, 10]
     idx, val = synth.uniform_tensor(dims, 3000, seed=7, device="cuda")
     g = torch.Generator(device="cuda").manual_seed(3)
@@ -341,8 +343,90 @@ def test_als_singular_gamma_reports_and_matches_pinv():
     st, fit = t.als_iter()
     assert st == dfacto.ESINGULAR
     ot = as_oracle(idx, val, dims)
-    st_o, Fo, lam_o = oracle.als_mode_update(ot, 0, [host(f) for f in F])
+    Fh = [host(f) for f in F]
+    st_m, _, _ = oracle.als_mode_update(ot, 0, Fh)
+    assert st_m == oracle.ESINGULAR
+    st_o, Fo, lam_o, fit_o = oracle.als_sweep(ot, Fh)
     assert st_o == oracle.ESINGULAR
+    after = [host(f) for f in t.factors()]
+    for m in range(3):
+        assert rel(after[m], Fo[m]) <= 1e-4, m
+        # the minimum-norm solution keeps the duplicated columns equal
+        np.testing.assert_allclose(after[m][:, 0], after[m][:, 1], rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(t.lam(), lam_o, rtol=1e-4)
+    assert abs(fit - fit_o) <= fit_tolerance(ot, Fo, lam_o), (fit, fit_o)
+
+
+@pytest.mark.parametrize("R", [4, 8])
+def test_als_singular_gamma_rank_deficient_start_stepwise(R):
+    """A start whose factors have rank R/2 (each column repeated): Gamma is
+    singular in every mode of the first sweep; three sweeps step-wise against
+    the oracle's pseudo-inverse path (factors and lambda to 1e-4)."""
+    dims = [60, 40, 30]
+    idx, val = synth.zipf_tensor(dims, 5000, [1.2, 1.1, 1.3], seed=77, device="cuda", values="cp",
+                                 R_true=4)
+    g = torch.Generator(device="cuda").manual_seed(78)
+    F = [torch.randn(d, R // 2, device="cuda", generator=g).repeat(1, 2) for d in dims]
+    t = dfacto.Tensor(idx, val, dims, rank=R)
+    t.set_factors(F)
+    ot = as_oracle(idx, val, dims)
+    for it in range(3):
+        before = [host(f) for f in t.factors()]
+        st, fit = t.als_iter()
+        st_o, Fo, lam_o, fit_o = oracle.als_sweep(ot, before)
+        assert st == (dfacto.ESINGULAR if st_o == oracle.ESINGULAR else dfacto.OK), (it, st, st_o)
+        after = [host(f) for f in t.factors()]
+        for m in range(3):
+            assert rel(after[m], Fo[m]) <= 1e-4, (it, m)
+        np.testing.assert_allclose(t.lam(), lam_o, rtol=1e-4, atol=1e-12)
+        assert abs(fit - fit_o) <= fit_tolerance(ot, Fo, lam_o), (it, fit, fit_o)
+
+
+@pytest.mark.parametrize("lam_reg,R", [(0.1, 8), (3.0, 10), (0.5, 32)])
+def test_als_regularized_stepwise(lam_reg, R):
+    """Regularized ALS (Appendix B, Eq. tensorapprx-ref-sol: F = N (Gamma +
+    lambda_reg I)^-1): four sweeps step-wise against the oracle's regularized
+    sweep from the factors the GPU held before each one."""
+    dims = [150, 120, 90]
+    t, idx, val, F = make(dims, 9000, R, seed=900 + R, zipf=[1.2, 1.2, 1.2], values="cp")
+    t = dfacto.Tensor(idx, val, dims, rank=R, lambda_reg=lam_reg)
+    t.set_factors(F)
+    ot = as_oracle(idx, val, dims)
+    for it in range(4):
+        before = [host(f) for f in t.factors()]
+        st, fit = t.als_iter()
+        assert st == dfacto.OK
+        st_o, Fo, lam_o, fit_o = oracle.als_sweep(ot, before, lam_reg)
+        assert st_o == oracle.OK
+        after = [host(f) for f in t.factors()]
+        for m in range(3):
+            assert rel(after[m], Fo[m]) <= 1e-4, (it, m)
+        np.testing.assert_allclose(t.lam(), lam_o, rtol=1e-4)
+        assert abs(fit - fit_o) <= fit_tolerance(ot, Fo, lam_o), (it, fit, fit_o)
+
+
+def test_als_regularized_singular_gamma_needs_no_pinv():
+    """The duplicated-column start that makes Gamma singular: with lambda_reg > 0
+    Gamma + lambda_reg I is positive definite, so the sweep takes the Cholesky
+    path (status OK) and equals the oracle's regularized sweep."""
+    dims = [30, 20, 10]
+    idx, val = synth.uniform_tensor(dims, 3000, seed=7, device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(3)
+    A = torch.randn(30, 2, device="cuda", generator=g)
+    b = torch.randn(20, 1, device="cuda", generator=g)
+    c = torch.randn(10, 1, device="cuda", generator=g)
+    F = [A, torch.cat([b, b], 1), torch.cat([c, c], 1)]
+    t = dfacto.Tensor(idx, val, dims, rank=2, lambda_reg=0.25)
+    t.set_factors(F)
+    st, fit = t.als_iter()
+    assert st == dfacto.OK
+    ot = as_oracle(idx, val, dims)
+    st_o, Fo, lam_o, fit_o = oracle.als_sweep(ot, [host(f) for f in F], 0.25)
+    assert st_o == oracle.OK
+    after = [host(f) for f in t.factors()]
+    for m in range(3):
+        assert rel(after[m], Fo[m]) <= 1e-4, m
+    np.testing.assert_allclose(t.lam(), lam_o, rtol=1e-4)
 
 
 def ray_tolerance(ot, F, G, alpha, lam_reg, eps=2e-6):

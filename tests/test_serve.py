@@ -233,14 +233,22 @@ def test_latency_stats():
 
 
 @pytest.mark.gpu
-def test_job_in_the_mix_equals_job_alone():
+@pytest.mark.parametrize("dtype_name,tol,fit_tol", [("f32", 1e-4, 1e-5), ("bf16", 1e-3, 1e-4)])
+def test_job_in_the_mix_equals_job_alone(dtype_name, tol, fit_tol):
     """Five jobs of mixed rank arrive together and in a burst; each is served
-    exactly three sweeps (tol = 0) in FP32.  Its factors equal the same job run
-    alone for three sweeps within 1e-4 normwise (the MTTKRP summation splits
-    differ between the batch and the single tensor, ~1e-6 per sweep)."""
+    exactly three sweeps (tol = 0).  Its factors equal the same job run alone
+    for three sweeps, with the same factor storage: within 1e-4 normwise with
+    FP32 factors (the MTTKRP summation splits differ between the batch and the
+    single tensor, ~1e-6 per sweep), within 1e-3 with BF16 factors as the
+    serving workload runs (a split difference can move a stored value by one
+    BF16 step, 2^-8 relative, in the rare entries that sit on a rounding
+    boundary).  The fits agree to 1e-5 (FP32) and 1e-4 (BF16) absolute, the
+    BF16 bar of the measurement plan."""
     import torch
 
     from paper_1406_4519_gb300 import dfacto, synth
+
+    fdt = dfacto.BF16 if dtype_name == "bf16" else dfacto.F32
 
     shapes = [([300, 200, 100], 20000, 8), ([500, 400, 300], 40000, 16), ([80, 60, 40], 3000, 10),
               ([700, 300, 200], 30000, 32), ([200, 200, 200], 10000, 16)]
@@ -257,17 +265,19 @@ def test_job_in_the_mix_equals_job_alone():
 
     jobs = [serve.JobSpec(i, arrivals[i], shapes[i][0], shapes[i][1], shapes[i][2], make=maker(i))
             for i in range(len(shapes))]
-    done = serve.serve(jobs, max_iters=3, tol=0.0, factor_dtype=dfacto.F32)
+    done = serve.serve(jobs, max_iters=3, tol=0.0, factor_dtype=fdt)
     assert len(done) == len(shapes)
     for job in done:
         i = job.spec.job_id
         assert job.iters == 3
         idx, val, F = maker(i)()
-        t = dfacto.Tensor(idx, val, shapes[i][0], rank=shapes[i][2])
+        t = dfacto.Tensor(idx, val, shapes[i][0], rank=shapes[i][2], factor_dtype=fdt)
         t.set_factors(F)
+        fit = None
         for _ in range(3):
-            t.als_iter()
+            st, fit = t.als_iter()
         alone = [f.double().cpu().numpy() for f in t.factors()]
         for m in range(3):
             got = job.result["factors"][m].double().numpy()
-            assert np.linalg.norm(got - alone[m]) <= 1e-4 * np.linalg.norm(alone[m]), (i, m)
+            assert np.linalg.norm(got - alone[m]) <= tol * np.linalg.norm(alone[m]), (i, m)
+        assert abs(job.fits[-1] - fit) <= fit_tol, (i, job.fits[-1], fit)
