@@ -77,6 +77,17 @@ typedef enum dfacto_dtype {
  *                 fibers of a few steps together; 0 lets the library choose.
  *                 Other values are refused (DFACTO_EINVAL).  Both compute the
  *                 same sums in the same order.
+ *   line_search   GD step size (dfacto_gd_iter): 0 (default) backtracking from
+ *                 min(2 alpha_prev, 1), halving until the Armijo condition holds
+ *                 (the rule read into Algorithm 5's "line search"); 1 the exact
+ *                 minimiser of f(theta - alpha grad) over alpha > 0.  Along the
+ *                 ray f is a polynomial of degree 6 in alpha (its cubic data term
+ *                 from one pass over the nonzeros, its model term from R x R
+ *                 Grams); the roots of its derivative are isolated in FP64 on
+ *                 the device and the local minimum with the smallest f is taken
+ *                 when it lowers f (otherwise the step falls back to
+ *                 backtracking).  The paper states no rule; this option is an
+ *                 addition.  Other values are refused (DFACTO_EINVAL).
  */
 typedef struct dfacto_options {
   int32_t rank;
@@ -85,7 +96,8 @@ typedef struct dfacto_options {
   int32_t seg_nnz;
   int32_t vec;
   int32_t walk;
-  int32_t reserved[5];
+  int32_t line_search;
+  int32_t reserved[4];
 } dfacto_options;
 
 /* Sizes of a built tensor. */
@@ -226,7 +238,9 @@ dfacto_status dfacto_als_iter(dfacto_t* h, double* fit_out);
  * the current point, then a backtracking line search -- alpha0 = min(2
  * alpha_prev, 1) (1 on the first step), accept the first alpha with
  * f(theta - alpha grad) <= f(theta) - 1e-4 alpha ||grad||^2, halving at most 100
- * times -- and the update theta <- theta - alpha grad.  f is the objective of
+ * times -- or, with the line_search option 1, the exact minimiser of
+ * f(theta - alpha grad) over alpha > 0, and the update theta <- theta - alpha
+ * grad.  f is the objective of
  * Eq. gd-obj-fn (regularized: Eq. gd-obj-fn-reg), evaluated in FP64.
  *   loss_out, alpha_out  host doubles, nullable; when both are NULL the call
  *                        does not synchronize.  loss_out gets f at the returned

@@ -82,6 +82,7 @@ def _load():
             "orc_loss": (D, [I64, P, P, P, I32, D, P, P, P]),
             "orc_gd_gradient": (I32, [I64, P, P, P, I32, D, P, P, P, P, P, P]),
             "orc_gd_step": (I32, [I64, P, P, P, I32, D, P, P, P, P, P, P]),
+            "orc_gd_ray_poly": (I32, [I64, P, P, P, I32, D, P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -282,3 +283,80 @@ def gd_step(t: Tensor, factors, alpha_prev: float = 0.0, lambda_reg: float = 0.0
 
 if __name__ == "__main__":  # pragma: no cover
     print(build(force="--force" in sys.argv))
+
+
+def gd_ray_poly(t: Tensor, factors, grads, lambda_reg: float = 0.0) -> np.ndarray:
+    """Coefficients c[0..6] of phi(alpha) = f(theta - alpha grad), lowest first
+    (orc_gd_ray_poly: the objective's terms expanded in alpha)."""
+    R = int(np.asarray(factors[0]).shape[1])
+    F = [_f64(factors[m], int(t.dims[m]), R) for m in range(3)]
+    G = [_f64(grads[m], int(t.dims[m]), R) for m in range(3)]
+    c = np.zeros(7, np.float64)
+    st = _load().orc_gd_ray_poly(t.nnz, _p(t.idx), _p(t.val), _p(t.dims), R, float(lambda_reg),
+                                 _p(F[0]), _p(F[1]), _p(F[2]), _p(G[0]), _p(G[1]), _p(G[2]),
+                                 _p(c))
+    if st != OK:
+        raise MemoryError("orc_gd_ray_poly status %d" % st)
+    return c
+
+
+def ray_minima(c) -> list:
+    """The local minima on alpha > 0 of the polynomial with coefficients c
+    (lowest first): the real positive roots of its derivative where the second
+    derivative is positive.  The roots come from the companion matrix of the
+    derivative after scaling alpha so that they lie in (0, 1] (Fujiwara's bound),
+    each polished by Newton's method on the unscaled derivative."""
+    c = np.asarray(c, np.float64)
+    d = np.array([(k + 1) * c[k + 1] for k in range(len(c) - 1)])
+    n = len(d) - 1
+    while n > 0 and d[n] == 0.0:
+        n -= 1
+    if n < 1:
+        return []
+    d = d[:n + 1]
+    terms = [abs(d[n - i] / d[n]) ** (1.0 / i) for i in range(1, n)]
+    terms.append((abs(d[0] / d[n]) / 2.0) ** (1.0 / n))
+    bound = 2.0 * max(terms)
+    if not np.isfinite(bound) or bound <= 0.0:
+        return []
+    scaled = d * bound ** np.arange(n + 1)
+    roots = np.roots(scaled[::-1]) * bound
+    dd = np.array([(k + 1) * d[k + 1] for k in range(n)])
+    out = []
+    for z in roots:
+        if abs(z.imag) > 1e-6 * abs(z) or z.real <= 0.0:
+            continue
+        a = float(z.real)
+        for _ in range(8):  # Newton on the derivative
+            fp, fpp = np.polyval(d[::-1], a), np.polyval(dd[::-1], a)
+            if fpp == 0.0:
+                break
+            step = fp / fpp
+            if not np.isfinite(step) or abs(step) > 0.5 * a:
+                break
+            a -= step
+        if np.polyval(dd[::-1], a) > 0.0:
+            out.append(a)
+    return sorted(set(out))
+
+
+def gd_step_exact(t: Tensor, factors, lambda_reg: float = 0.0, alpha_prev: float = 0.0):
+    """GD step with the exact line search: alpha = the minimiser of
+    phi(alpha) = f(theta - alpha grad) over alpha > 0 (the local minimum of the
+    degree-6 polynomial phi with the smallest value of f, evaluated from the
+    definition with orc_loss), taken when it lowers f; otherwise the
+    backtracking step of gd_step.  Returns (status, [A,B,C] updated copies,
+    alpha, loss, g2)."""
+    R, F = _factors_rw(t, factors)
+    G = gd_gradient(t, F, lambda_reg)
+    g2 = float(sum(np.sum(g * g) for g in G))
+    f0 = loss(t, F, lambda_reg)
+    best, best_f = None, f0
+    for a in ray_minima(gd_ray_poly(t, F, G, lambda_reg)):
+        fa = loss(t, [F[m] - a * G[m] for m in range(3)], lambda_reg)
+        if fa < best_f:
+            best, best_f = a, fa
+    if best is None:
+        return gd_step(t, F, alpha_prev, lambda_reg)
+    return OK, [F[m] - best * G[m] for m in range(3)], best, best_f, g2
+

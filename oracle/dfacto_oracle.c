@@ -642,3 +642,82 @@ int orc_gd_step(int64_t nnz, const int32_t* idx, const float* val, const int32_t
   }
   return st;
 }
+
+/*
+ * The GD objective along the search ray, phi(alpha) = f(A - alpha GA,
+ * B - alpha GB, C - alpha GC) with f of Eq. gd-obj-fn (regularized form
+ * Eq. gd-obj-fn-reg), is a polynomial of degree 6 in alpha.  Its coefficients
+ * coef[0..6] are taken term by term from the definition:
+ *   1/2 ||X||^2;
+ *   -<X, [[.]]>: each observed entry contributes x * sum_r of the product of
+ *     three linear polynomials (F_n[i_n, r] - alpha G_n[i_n, r]), n = A, B, C;
+ *   +1/2 ||[[.]]||^2 = 1/2 sum_rs prod_n M_n(alpha)[r, s] with the Gram
+ *     M_n(alpha) = (F_n - alpha G_n)^T (F_n - alpha G_n) (Eq. kr-product),
+ *     a quadratic in alpha entry by entry;
+ *   +1/2 lambda_reg sum_n ||F_n - alpha G_n||^2.
+ * Used by the exact line search, an option beside the backtracking rule.
+ */
+int orc_gd_ray_poly(int64_t nnz, const int32_t* idx, const float* val, const int32_t* dims,
+                    int R, double lambda_reg, const double* A, const double* B,
+                    const double* C, const double* GA, const double* GB, const double* GC,
+                    double* coef) {
+  const double* F[3] = {A, B, C};
+  const double* G[3] = {GA, GB, GC};
+  for (int k = 0; k < 7; ++k) coef[k] = 0.0;
+  coef[0] = 0.5 * orc_norm2(nnz, val);
+  /* data term */
+  for (int64_t t = 0; t < nnz; ++t) {
+    const double x = (double)val[t];
+    for (int r = 0; r < R; ++r) {
+      double p[4] = {1.0, 0.0, 0.0, 0.0};
+      for (int n = 0; n < 3; ++n) {
+        const int64_t row = idx[(int64_t)n * nnz + t];
+        const double u0 = F[n][row * R + r], u1 = -G[n][row * R + r];
+        double q[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k = 0; k < 3; ++k) {
+          q[k] += p[k] * u0;
+          q[k + 1] += p[k] * u1;
+        }
+        for (int k = 0; k < 4; ++k) p[k] = q[k];
+      }
+      for (int k = 0; k < 4; ++k) coef[k] -= x * p[k];
+    }
+  }
+  /* model term: Grams of F_n - alpha G_n as quadratics */
+  double* M[3];
+  for (int n = 0; n < 3; ++n) {
+    M[n] = (double*)calloc((size_t)3 * R * R, sizeof(double));
+    if (!M[n]) return ORC_ENOMEM;
+    for (int64_t i = 0; i < dims[n]; ++i)
+      for (int r = 0; r < R; ++r)
+        for (int s = 0; s < R; ++s) {
+          const double fr = F[n][i * R + r], fs = F[n][i * R + s];
+          const double gr = G[n][i * R + r], gs = G[n][i * R + s];
+          M[n][r * R + s] += fr * fs;
+          M[n][R * R + r * R + s] -= fr * gs + gr * fs;
+          M[n][2 * R * R + r * R + s] += gr * gs;
+        }
+  }
+  for (int e = 0; e < R * R; ++e) {
+    double p[7] = {1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int deg = 0;
+    for (int n = 0; n < 3; ++n) {
+      double q[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int i = 0; i <= deg; ++i)
+        for (int j = 0; j < 3; ++j) q[i + j] += p[i] * M[n][j * R * R + e];
+      deg += 2;
+      for (int i = 0; i <= deg; ++i) p[i] = q[i];
+    }
+    for (int k = 0; k < 7; ++k) coef[k] += 0.5 * p[k];
+  }
+  for (int n = 0; n < 3; ++n) free(M[n]);
+  /* ridge */
+  if (lambda_reg != 0.0)
+    for (int n = 0; n < 3; ++n)
+      for (int64_t t = 0; t < (int64_t)dims[n] * R; ++t) {
+        coef[0] += 0.5 * lambda_reg * F[n][t] * F[n][t];
+        coef[1] -= lambda_reg * F[n][t] * G[n][t];
+        coef[2] += 0.5 * lambda_reg * G[n][t] * G[n][t];
+      }
+  return ORC_OK;
+}

@@ -282,6 +282,7 @@ dfacto_status dfacto_build(const int32_t* idx, const float* val, int64_t nnz, co
   if (opt.vec != 0 && R % opt.vec != 0) return DFACTO_EINVAL;
   if (opt.seg_nnz < 0 || opt.seg_nnz > kMaxSeg) return DFACTO_EINVAL;
   if (opt.walk < 0 || opt.walk > 2) return DFACTO_EINVAL;
+  if (opt.line_search != 0 && opt.line_search != 1) return DFACTO_EINVAL;
 
   dfacto_t* h = new (std::nothrow) dfacto_handle();
   if (!h) return DFACTO_ENOMEM;

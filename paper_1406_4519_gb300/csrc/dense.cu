@@ -762,12 +762,91 @@ __global__ void __launch_bounds__(kT) gd_scalars(const double* __restrict__ spar
 //   P(alpha) = <X, [[A - aGA, B - aGB, C - aGC]]> = sum_S (-alpha)^|S| T_S
 //   M_n(alpha) = P0_n - alpha P1_n + alpha^2 P2_n   (Gram of F_n - alpha G_n)
 //   Q(alpha) = sum_rs prod_n M_n(alpha)_rs         (||[[.]]||^2, Eq. kr-product)
-// Backtracking as specified in dfacto.h; one CTA.
+// f is a polynomial of degree 6 in alpha.
+
+// Horner evaluation of c[0] + c[1] x + ... + c[n] x^n.
+__device__ __forceinline__ double poly_eval(const double* c, int n, double x) {
+  double v = c[n];
+  for (int k = n - 1; k >= 0; --k) v = fma(v, x, c[k]);
+  return v;
+}
+
+// The root of the monotone p (degree n) in [a, b], where p(a) and p(b) have
+// opposite signs, by bisection down to adjacent doubles.
+__device__ double bisect_root(const double* c, int n, double a, double b) {
+  const double fa = poly_eval(c, n, a);
+  for (int it = 0; it < 2200; ++it) {
+    const double m = 0.5 * (a + b);
+    if (m <= a || m >= b) break;
+    const double fm = poly_eval(c, n, m);
+    if (fm == 0.0) return m;
+    if ((fm < 0.0) == (fa < 0.0)) a = m;
+    else b = m;
+  }
+  return 0.5 * (a + b);
+}
+
+constexpr int kPolyMax = 5;  // degree of f'
+
+// Real roots of p (coefficients c[0..n], 1 <= n <= kPolyMax, c[n] != 0) in the
+// open interval (lo, hi), ascending, by the derivative sequence: the roots of
+// p^(k+1) split (lo, hi) into pieces on which p^(k) is monotone, and each
+// piece with a sign change holds exactly one root of p^(k), found by
+// bisection.  Returns the count.
+__device__ int poly_roots(const double* c, int n, double lo, double hi, double* roots) {
+  double D[kPolyMax + 1][kPolyMax + 1];  // D[k] = k-th derivative, degree n - k
+  for (int i = 0; i <= n; ++i) D[0][i] = c[i];
+  for (int k = 1; k < n; ++k)
+    for (int i = 0; i <= n - k; ++i) D[k][i] = D[k - 1][i + 1] * (double)(i + 1);
+  double r[kPolyMax + 2];
+  int nr = 0;
+  {  // the (n-1)-th derivative is linear
+    const double* L = D[n - 1];
+    const double x = -L[0] / L[1];
+    if (x > lo && x < hi) r[nr++] = x;
+  }
+  for (int k = n - 2; k >= 0; --k) {
+    const double* P = D[k];
+    const int deg = n - k;
+    double pts[kPolyMax + 3];
+    int np = 0;
+    pts[np++] = lo;
+    for (int i = 0; i < nr; ++i) pts[np++] = r[i];
+    pts[np++] = hi;
+    double nxt[kPolyMax + 2];
+    int nn = 0;
+    double va = poly_eval(P, deg, pts[0]);
+    for (int i = 0; i + 1 < np; ++i) {
+      const double vb = poly_eval(P, deg, pts[i + 1]);
+      if (va == 0.0 && i > 0) {
+        if (nn == 0 || nxt[nn - 1] != pts[i]) nxt[nn++] = pts[i];
+      } else if ((va < 0.0 && vb > 0.0) || (va > 0.0 && vb < 0.0)) {
+        nxt[nn++] = bisect_root(P, deg, pts[i], pts[i + 1]);
+      }
+      va = vb;
+    }
+    nr = nn;
+    for (int i = 0; i < nn; ++i) r[i] = nxt[i];
+  }
+  for (int i = 0; i < nr; ++i) roots[i] = r[i];
+  return nr;
+}
+
+// One CTA.  exact == 0: backtracking as specified in dfacto.h.  exact == 1:
+// the exact minimiser over alpha > 0 -- the coefficients of f are formed in
+// FP64 from the same terms, the real roots of f' on (0, B] (B: Fujiwara's
+// bound on the roots of f') are isolated, the local minima among them are
+// evaluated in the factored form above, and the smallest is taken when it
+// lowers f; when there is none (possible only through rounding of a
+// degenerate ray), the step falls back to backtracking.
 __global__ void __launch_bounds__(256) gd_line_search(const double* __restrict__ mats, int R,
                                                      double lambda_reg, double* __restrict__ scal,
-                                                     int32_t* __restrict__ lsfail) {
+                                                     int32_t* __restrict__ lsfail, int exact) {
   __shared__ double red[256];
   __shared__ double s_q;
+  __shared__ double s_qc[256][7];
+  __shared__ double s_cand[kPolyMax];
+  __shared__ int s_ncand;
   const int tid = threadIdx.x;
   const int RR = R * R;
   auto Q = [&](double a) {
@@ -814,17 +893,100 @@ __global__ void __launch_bounds__(256) gd_line_search(const double* __restrict__
   };
   const double f0 = f(0.0);
   const double g2 = scal[kG2];
-  const double prev = scal[kAlpha];
-  double alpha = prev > 0.0 ? fmin(2.0 * prev, 1.0) : 1.0;
   bool ok = false;
-  double fa = f0;
-  for (int trial = 0; trial < kLineSearchTrials; ++trial) {
-    fa = f(alpha);
-    if (fa <= f0 - 1e-4 * alpha * g2) {
-      ok = true;
-      break;
+  double alpha = 0.0, fa = f0;
+  if (exact) {
+    // coefficients of Q: per entry the product of three quadratics
+    double q[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int e = tid; e < RR; e += blockDim.x) {
+      double p[7] = {1, 0, 0, 0, 0, 0, 0};
+      int deg = 0;
+      for (int n = 0; n < 3; ++n) {
+        const double* P = mats + (size_t)n * 3 * RR;
+        const double u[3] = {P[e], -P[RR + e], P[2 * RR + e]};
+        double np_[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int i = 0; i <= deg; ++i)
+          for (int j = 0; j < 3; ++j) np_[i + j] += p[i] * u[j];
+        deg += 2;
+        for (int i = 0; i <= deg; ++i) p[i] = np_[i];
+      }
+      for (int k = 0; k < 7; ++k) q[k] += p[k];
     }
-    alpha *= 0.5;
+    for (int k = 0; k < 7; ++k) s_qc[tid][k] = q[k];
+    __syncthreads();
+    if (tid == 0) {
+      double qc[7] = {0, 0, 0, 0, 0, 0, 0};
+      for (int i = 0; i < (int)blockDim.x; ++i)
+        for (int k = 0; k < 7; ++k) qc[k] += s_qc[i][k];
+      double tr[3] = {0, 0, 0};
+      for (int n = 0; n < 3; ++n) {
+        const double* P = mats + (size_t)n * 3 * RR;
+        for (int r = 0; r < R; ++r) {
+          tr[0] += P[r * R + r];
+          tr[1] += P[RR + r * R + r];
+          tr[2] += P[2 * RR + r * R + r];
+        }
+      }
+      double c[7];
+      c[0] = 0.5 * (nx2 - 2.0 * t0 + qc[0]) + 0.5 * lambda_reg * tr[0];
+      c[1] = 0.5 * (2.0 * t1 + qc[1]) - 0.5 * lambda_reg * tr[1];
+      c[2] = 0.5 * (-2.0 * t2 + qc[2]) + 0.5 * lambda_reg * tr[2];
+      c[3] = 0.5 * (2.0 * t3 + qc[3]);
+      c[4] = 0.5 * qc[4];
+      c[5] = 0.5 * qc[5];
+      c[6] = 0.5 * qc[6];
+      double d[kPolyMax + 1];
+      for (int k = 0; k <= kPolyMax; ++k) d[k] = (double)(k + 1) * c[k + 1];
+      int n = kPolyMax;
+      while (n > 0 && d[n] == 0.0) --n;
+      int nc = 0;
+      if (n >= 1) {
+        // Fujiwara's bound on |roots|: 2 max_i |d_{n-i} / d_n|^(1/i), last term halved
+        double B = 0.0;
+        for (int i = 1; i <= n; ++i) {
+          double v = fabs(d[n - i] / d[n]);
+          if (i == n) v *= 0.5;
+          B = fmax(B, pow(v, 1.0 / i));
+        }
+        B = 2.0 * B;
+        if (isfinite(B) && B > 0.0) {
+          double roots[kPolyMax];
+          const int nr = poly_roots(d, n, 0.0, B * (1.0 + 1e-12), roots);
+          for (int i = 0; i < nr; ++i) {
+            // a local minimum: f' changes from negative to positive
+            const double lo = i == 0 ? 0.0 : roots[i - 1];
+            const double hi = i + 1 < nr ? roots[i + 1] : 2.0 * B + 1.0;
+            const double left = poly_eval(d, n, 0.5 * (lo + roots[i]));
+            const double right = poly_eval(d, n, 0.5 * (roots[i] + hi));
+            if (left < 0.0 && right > 0.0 && roots[i] > 0.0) s_cand[nc++] = roots[i];
+          }
+        }
+      }
+      s_ncand = nc;
+    }
+    __syncthreads();
+    const int nc = s_ncand;
+    for (int i = 0; i < nc; ++i) {
+      const double a = s_cand[i];
+      const double v = f(a);  // all threads (block-wide Q)
+      if (v < fa) {  // fa starts at f(0): only a decrease is taken
+        ok = true;
+        fa = v;
+        alpha = a;
+      }
+    }
+  }
+  if (!ok) {
+    const double prev = scal[kAlpha];
+    alpha = prev > 0.0 ? fmin(2.0 * prev, 1.0) : 1.0;
+    for (int trial = 0; trial < kLineSearchTrials; ++trial) {
+      fa = f(alpha);
+      if (fa <= f0 - 1e-4 * alpha * g2) {
+        ok = true;
+        break;
+      }
+      alpha *= 0.5;
+    }
   }
   if (tid == 0) {
     if (ok) {
@@ -1796,7 +1958,8 @@ dfacto_status gd_step_rows(dfacto_t* h) {
     DF_CUDA(h, cudaGetLastError());
   }
   if ((st = dual_pass(h)) != DFACTO_OK) return st;
-  gd_line_search<<<1, 256, 0, s>>>(h->gd_mats, R, h->lambda_reg, h->scal, h->flags + kFlagLsFail);
+  gd_line_search<<<1, 256, 0, s>>>(h->gd_mats, R, h->lambda_reg, h->scal, h->flags + kFlagLsFail,
+                                   h->opt.line_search);
   DF_COUNT();
   for (int m = 0; m < 3; ++m) {
     const int64_t rows = h->dims[m];
@@ -1853,7 +2016,8 @@ dfacto_status gd_step_T(dfacto_t* h) {
       return st;
   }
   if ((st = dual_pass(h)) != DFACTO_OK) return st;
-  gd_line_search<<<1, 256, 0, s>>>(h->gd_mats, R, h->lambda_reg, h->scal, h->flags + kFlagLsFail);
+  gd_line_search<<<1, 256, 0, s>>>(h->gd_mats, R, h->lambda_reg, h->scal, h->flags + kFlagLsFail,
+                                   h->opt.line_search);
   DF_COUNT();
   for (int m = 0; m < 3; ++m) {
     const int64_t n = (int64_t)h->dims[m] * R;

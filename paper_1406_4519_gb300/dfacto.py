@@ -21,6 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdfacto.so")
 
 OK, EINVAL, ERANGE, EDUP, ENOMEM, ECUDA, ESINGULAR, ELSFAIL, ETIMEOUT, EINTERNAL = range(10)
+BACKTRACKING, EXACT = 0, 1  # dfacto_options.line_search
 F32, BF16, F64 = 0, 1, 2
 _DTYPE = {torch.float32: F32, torch.bfloat16: BF16, torch.float64: F64}
 
@@ -35,7 +36,7 @@ class dfacto_options(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int32), ("factor_dtype", ctypes.c_int32),
                 ("lambda_reg", ctypes.c_double), ("seg_nnz", ctypes.c_int32),
                 ("vec", ctypes.c_int32), ("walk", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("line_search", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class dfacto_info(ctypes.Structure):
@@ -140,7 +141,8 @@ def _stream_ptr(stream) -> Optional[int]:
 
 
 def dfacto_options_init(rank: int, factor_dtype: int = F32, lambda_reg: float = 0.0,
-                        seg_nnz: int = 0, vec: int = 0, walk: int = 0) -> dfacto_options:
+                        seg_nnz: int = 0, vec: int = 0, walk: int = 0,
+                        line_search: int = 0) -> dfacto_options:
     opt = dfacto_options()
     load().dfacto_options_init(ctypes.byref(opt), int(rank))
     opt.factor_dtype = factor_dtype
@@ -148,6 +150,7 @@ def dfacto_options_init(rank: int, factor_dtype: int = F32, lambda_reg: float = 
     opt.seg_nnz = int(seg_nnz)
     opt.vec = int(vec)
     opt.walk = int(walk)
+    opt.line_search = int(line_search)
     return opt
 
 
@@ -300,10 +303,11 @@ class Tensor:
 
     def __init__(self, idx, val, dims, rank: int, factor_dtype: int = F32,
                  lambda_reg: float = 0.0, seg_nnz: int = 0, vec: int = 0, walk: int = 0,
-                 stream=None):
+                 line_search: int = 0, stream=None):
         self.dims = [int(d) for d in dims]
         self.rank = int(rank)
-        self.opt = dfacto_options_init(rank, factor_dtype, lambda_reg, seg_nnz, vec, walk)
+        self.opt = dfacto_options_init(rank, factor_dtype, lambda_reg, seg_nnz, vec, walk,
+                                       line_search)
         self.h = dfacto_build(idx, val, dims, self.opt, stream)
 
     def __del__(self):

@@ -47,9 +47,9 @@ def test_struct_layouts_match_header(tmp_path, lib):
 #include <stddef.h>
 #include "dfacto.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\\n", sizeof(dfacto_options), offsetof(dfacto_options, lambda_reg),
+  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(dfacto_options), offsetof(dfacto_options, lambda_reg),
          offsetof(dfacto_options, seg_nnz), offsetof(dfacto_options, vec),
-         offsetof(dfacto_options, walk));
+         offsetof(dfacto_options, walk), offsetof(dfacto_options, line_search));
   printf("%zu %zu %zu %zu\\n", sizeof(dfacto_info), offsetof(dfacto_info, nnz),
          offsetof(dfacto_info, norm_x2), offsetof(dfacto_info, vec));
   printf("%zu %zu\\n", sizeof(dfacto_csr_view), offsetof(dfacto_csr_view, nz_val));
@@ -64,7 +64,7 @@ int main(void) {
     got = subprocess.check_output([str(exe)]).decode().split()
     want = [ctypes.sizeof(dfacto.dfacto_options), dfacto.dfacto_options.lambda_reg.offset,
             dfacto.dfacto_options.seg_nnz.offset, dfacto.dfacto_options.vec.offset,
-            dfacto.dfacto_options.walk.offset,
+            dfacto.dfacto_options.walk.offset, dfacto.dfacto_options.line_search.offset,
             ctypes.sizeof(dfacto.dfacto_info), dfacto.dfacto_info.nnz.offset,
             dfacto.dfacto_info.norm_x2.offset, dfacto.dfacto_info.vec.offset,
             ctypes.sizeof(dfacto.dfacto_csr_view), dfacto.dfacto_csr_view.nz_val.offset,
@@ -102,6 +102,10 @@ def test_host_side_argument_checks(lib):
     opt = dfacto.dfacto_options_init(8, seg_nnz=4097)  # segments of at most 4096
     assert lib.dfacto_build(None, None, 0, dims, ctypes.byref(opt), None,
                             ctypes.byref(out)) == dfacto.EINVAL
+    for ls in (-1, 2):  # line searches 0 (backtracking) and 1 (exact) exist
+        opt = dfacto.dfacto_options_init(8, line_search=ls)
+        assert lib.dfacto_build(None, None, 0, dims, ctypes.byref(opt), None,
+                                ctypes.byref(out)) == dfacto.EINVAL
     for walk in (-1, 3, 4):  # walks 0 (library's choice), 1 and 2 exist
         opt = dfacto.dfacto_options_init(8, walk=walk)
         assert lib.dfacto_build(None, None, 0, dims, ctypes.byref(opt), None,

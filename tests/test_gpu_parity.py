@@ -449,6 +449,66 @@ def ray_tolerance(ot, F, G, alpha, lam_reg, eps=2e-6):
     return eps * (2 * T + Qabs + ridge) / 2 + 1e-9
 
 
+def ray_slope_tolerance(ot, F, G, alpha, lam_reg, eps=2e-6):
+    """Rounding bound of f'(alpha) formed from the same FP32-accumulated terms
+    as ray_tolerance: the derivative of each term's magnitude along the ray,
+    times eps."""
+    import itertools
+    T = 0.0
+    for S in itertools.product([0, 1], repeat=3):
+        k = sum(S)
+        if k:
+            T += k * alpha ** (k - 1) * abs(oracle.inner(ot, [G[m] if S[m] else F[m] for m in range(3)]))
+    a0 = [np.abs(F[m].T @ F[m]) for m in range(3)]
+    a1 = [np.abs(F[m].T @ G[m] + G[m].T @ F[m]) for m in range(3)]
+    a2 = [np.abs(G[m].T @ G[m]) for m in range(3)]
+    M = [a0[m] + alpha * a1[m] + alpha ** 2 * a2[m] for m in range(3)]
+    dM = [a1[m] + 2 * alpha * a2[m] for m in range(3)]
+    dQ = float(np.sum(dM[0] * M[1] * M[2] + M[0] * dM[1] * M[2] + M[0] * M[1] * dM[2]))
+    ridge = lam_reg * sum(2 * float(np.sum(np.abs(f * g))) + 2 * alpha * float(np.sum(g * g))
+                          for f, g in zip(F, G))
+    return eps * (2 * T + dQ + ridge) / 2
+
+
+@pytest.mark.parametrize("R", [8, 10, 32])
+@pytest.mark.parametrize("lam_reg", [0.0, 0.5])
+def test_gd_exact_line_search_stepwise(lam_reg, R):
+    """GD with the exact line search (line_search = 1), each step from the GPU's
+    state against the oracle's exact step (the global minimiser of the degree-6
+    polynomial f(theta - alpha grad), evaluated from the definition): alpha agrees
+    within the bound a rounding error of f' moves a minimum (|d f'| / f''), the
+    objective within ray_tolerance, the factors to 1e-5 normwise plus what the
+    alpha difference moves them.  Every step lowers the objective, by at least
+    as much as the backtracking step would from the same point."""
+    dims = [120, 90, 60]
+    t, idx, val, F = make(dims, 8000, R, seed=800 + R, zipf=[1.2, 1.1, 1.3], values="cp")
+    t = dfacto.Tensor(idx, val, dims, rank=R, lambda_reg=lam_reg, line_search=dfacto.EXACT)
+    t.set_factors(F)
+    ot = as_oracle(idx, val, dims)
+    prev = oracle.loss(ot, [host(f) for f in F], lam_reg)
+    for it in range(4):
+        before = [host(f) for f in t.factors()]
+        st, loss, alpha = t.gd_iter()
+        st_o, Fo, alpha_o, loss_o, g2 = oracle.gd_step_exact(ot, before, lam_reg)
+        assert st == dfacto.OK and st_o == oracle.OK
+        G = oracle.gd_gradient(ot, before, lam_reg)
+        c = oracle.gd_ray_poly(ot, before, G, lam_reg)
+        curv = sum(k * (k - 1) * c[k] * alpha_o ** (k - 2) for k in range(2, 7))
+        assert curv > 0
+        tol_a = 2 * ray_slope_tolerance(ot, before, G, alpha_o, lam_reg) / curv + 1e-12 * alpha_o
+        assert abs(alpha - alpha_o) <= tol_a, (it, alpha, alpha_o, tol_a)
+        tol = ray_tolerance(ot, before, G, alpha_o, lam_reg) + 0.5 * curv * tol_a ** 2
+        assert abs(loss - loss_o) <= tol, (it, loss, loss_o, tol)
+        after = [host(f) for f in t.factors()]
+        for m in range(3):
+            shift = tol_a * np.linalg.norm(G[m]) / max(np.linalg.norm(Fo[m]), 1e-300)
+            assert rel(after[m], Fo[m]) <= 1e-5 + shift, (it, m)
+        st_b, Fb, alpha_b, loss_b, _ = oracle.gd_step(ot, before, 0.0, lam_reg)
+        assert loss_o <= loss_b + 1e-12 * abs(loss_b)
+        assert loss_o < prev
+        prev = loss_o
+
+
 @pytest.mark.parametrize("R", [8, 10, 12])
 @pytest.mark.parametrize("lam_reg", [0.0, 0.5])
 def test_gd_stepwise(lam_reg, R):

@@ -44,6 +44,11 @@ MUTATIONS = {
                                     "for (int k = r + 1; k < R; ++k) s -= L[r * R + k] * X[i * R + k];"),
     "jacobi_rotation_sign": ("double c = 1.0 / sqrt(t * t + 1.0), s = t * c;",
                              "double c = 1.0 / sqrt(t * t + 1.0), s = -t * c;"),
+    "ray_step_sign": ("const double u0 = F[n][row * R + r], u1 = -G[n][row * R + r];",
+                      "const double u0 = F[n][row * R + r], u1 = G[n][row * R + r];"),
+    "ray_gram_cross_term_halved": ("M[n][R * R + r * R + s] -= fr * gs + gr * fs;",
+                                   "M[n][R * R + r * R + s] -= fr * gs;"),
+    "ray_ridge_slope_dropped": ("        coef[1] -= lambda_reg * F[n][t] * G[n][t];\n", "\n"),
 }
 
 

@@ -437,6 +437,54 @@ def test_gd_step_armijo_backtracking(seed, scale):
         assert start_matters > 0  # starting at 1 instead of 2 alpha_prev would differ
 
 
+@pytest.mark.parametrize("seed,lam_reg", [(41, 0.0), (42, 0.4)])
+def test_gd_ray_polynomial_is_the_loss_along_the_ray(seed, lam_reg):
+    """The seven coefficients of phi(alpha) = f(theta - alpha grad) reproduce the
+    dense loss (computed here from the dense tensor, independently of the
+    oracle) at step sizes from 1e-4 to 10."""
+    rng = np.random.default_rng(seed)
+    dims = [8, 7, 6]
+    t = random_sparse(rng, dims, 0.3)
+    X = dense_from_coo(t.idx, t.val, dims)
+    F = [rng.standard_normal((d, 3)) for d in dims]
+    G = oracle.gd_gradient(t, F, lam_reg)
+    c = oracle.gd_ray_poly(t, F, G, lam_reg)
+    for a in [0.0, 1e-4, 3e-3, 0.02, 0.1, 0.7, 2.5, 10.0]:
+        want = dense_loss(X, [f - a * g for f, g in zip(F, G)], lam_reg)
+        assert np.polyval(c[::-1], a) == pytest.approx(want, rel=1e-10), a
+
+
+@pytest.mark.parametrize("seed,lam_reg,scale", [(43, 0.0, 1.0), (44, 0.4, 1.0), (45, 0.0, 6.0)])
+def test_gd_exact_step_is_the_minimiser_on_the_ray(seed, lam_reg, scale):
+    """The exact step's alpha is the global minimiser of the dense loss along the
+    ray: no point of a brute-force grid (log-spaced over eight decades around
+    alpha and linear up to 4 alpha) is lower; the new point is theta - alpha
+    grad with the loss it reports; it is at least as low as the backtracking
+    step's; the loss keeps decreasing over the steps."""
+    rng = np.random.default_rng(seed)
+    dims = [8, 7, 6]
+    t = random_sparse(rng, dims, 0.3)
+    t = oracle.Tensor(t.idx, t.val * scale, dims)
+    X = dense_from_coo(t.idx, t.val, dims)
+    F = [scale * rng.standard_normal((d, 3)) for d in dims]
+    prev = dense_loss(X, F, lam_reg)
+    for it in range(4):
+        G = oracle.gd_gradient(t, F, lam_reg)
+        st, F2, alpha, lo, g2 = oracle.gd_step_exact(t, F, lam_reg)
+        assert st == oracle.OK and alpha > 0
+        for m in range(3):
+            np.testing.assert_allclose(F2[m], F[m] - alpha * G[m], rtol=1e-14, atol=1e-14)
+        assert lo == pytest.approx(dense_loss(X, F2, lam_reg), rel=1e-12)
+        grid = np.concatenate([np.geomspace(alpha * 1e-4, alpha * 1e4, 1601),
+                               np.linspace(0.0, 4 * alpha, 801)])
+        best = min(dense_loss(X, [f - a * g for f, g in zip(F, G)], lam_reg) for a in grid)
+        assert lo <= best + 1e-12 * abs(best)
+        st_b, Fb, ab, lob, _ = oracle.gd_step(t, F, 0.0, lam_reg)
+        assert lo <= lob + 1e-12 * abs(lob)
+        assert lo < prev
+        F, prev = F2, lo
+
+
 def test_gd_line_search_failure_leaves_factors():
     """When no trial passes the test (here a NaN value makes every comparison
     false), the step reports ELSFAIL and leaves the factors and alpha as they were."""
