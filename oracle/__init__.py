@@ -83,6 +83,10 @@ def _load():
             "orc_gd_gradient": (I32, [I64, P, P, P, I32, D, P, P, P, P, P, P]),
             "orc_gd_step": (I32, [I64, P, P, P, I32, D, P, P, P, P, P, P]),
             "orc_gd_ray_poly": (I32, [I64, P, P, P, I32, D, P, P, P, P, P, P, P]),
+            "orc_joint_loss": (D, [I64, P, P, I64, P, P, P, I32, D, D, P, P, P]),
+            "orc_joint_gradient": (I32, [I64, P, P, I64, P, P, P, I32, D, D, P, P, P, P, P, P]),
+            "orc_joint_als_sweep": (I32, [I64, P, P, I64, P, P, P, I32, D, D, P, P, P]),
+            "orc_joint_gd_step": (I32, [I64, P, P, I64, P, P, P, I32, D, D, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -359,4 +363,54 @@ def gd_step_exact(t: Tensor, factors, lambda_reg: float = 0.0, alpha_prev: float
     if best is None:
         return gd_step(t, F, alpha_prev, lambda_reg)
     return OK, [F[m] - best * G[m] for m in range(3)], best, best_f, g2
+
+
+class Ratings:
+    """Observed ratings of the joint model (Appendix F): yidx int32[2, nnzY]
+    (user i, item j), yval float32[nnzY]."""
+
+    def __init__(self, yidx, yval):
+        self.idx = np.ascontiguousarray(np.asarray(yidx, dtype=np.int32).reshape(2, -1))
+        self.val = np.ascontiguousarray(np.asarray(yval, dtype=np.float32).reshape(-1))
+        self.nnz = int(self.val.shape[0])
+
+
+def joint_loss(y: Ratings, t: Tensor, factors, mu: float, lam: float) -> float:
+    R = int(np.asarray(factors[0]).shape[1])
+    F = [_f64(factors[m], int(t.dims[m]), R) for m in range(3)]
+    return _load().orc_joint_loss(y.nnz, _p(y.idx), _p(y.val), t.nnz, _p(t.idx), _p(t.val),
+                                  _p(t.dims), R, float(mu), float(lam), _p(F[0]), _p(F[1]), _p(F[2]))
+
+
+def joint_gradient(y: Ratings, t: Tensor, factors, mu: float, lam: float):
+    R = int(np.asarray(factors[0]).shape[1])
+    F = [_f64(factors[m], int(t.dims[m]), R) for m in range(3)]
+    G = [np.zeros_like(F[m]) for m in range(3)]
+    st = _load().orc_joint_gradient(y.nnz, _p(y.idx), _p(y.val), t.nnz, _p(t.idx), _p(t.val),
+                                    _p(t.dims), R, float(mu), float(lam), _p(F[0]), _p(F[1]),
+                                    _p(F[2]), _p(G[0]), _p(G[1]), _p(G[2]))
+    if st != OK:
+        raise MemoryError("orc_joint_gradient status %d" % st)
+    return G
+
+
+def joint_als_sweep(y: Ratings, t: Tensor, factors, mu: float, lam: float):
+    """Returns (status, [A,B,C] updated copies)."""
+    R, F = _factors_rw(t, factors)
+    st = _load().orc_joint_als_sweep(y.nnz, _p(y.idx), _p(y.val), t.nnz, _p(t.idx), _p(t.val),
+                                     _p(t.dims), R, float(mu), float(lam), _p(F[0]), _p(F[1]),
+                                     _p(F[2]))
+    return st, F
+
+
+def joint_gd_step(y: Ratings, t: Tensor, factors, mu: float, lam: float, alpha_prev: float = 0.0):
+    """Returns (status, [A,B,C] updated copies, alpha, loss, g2)."""
+    R, F = _factors_rw(t, factors)
+    a = np.array([alpha_prev], np.float64)
+    lo = np.zeros(1, np.float64)
+    g2 = np.zeros(1, np.float64)
+    st = _load().orc_joint_gd_step(y.nnz, _p(y.idx), _p(y.val), t.nnz, _p(t.idx), _p(t.val),
+                                   _p(t.dims), R, float(mu), float(lam), _p(F[0]), _p(F[1]),
+                                   _p(F[2]), _p(a), _p(lo), _p(g2))
+    return st, F, float(a[0]), float(lo[0]), float(g2[0])
 

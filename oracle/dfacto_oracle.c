@@ -721,3 +721,200 @@ int orc_gd_ray_poly(int64_t nnz, const int32_t* idx, const float* val, const int
       }
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Joint matrix completion and tensor factorization (Appendix F).            */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * The model shares the user factor A (rows i) and the item factor B (rows j)
+ * between a ratings matrix Y (observed entries (i, j) in Omega^Y, yidx[0][t] =
+ * i, yidx[1][t] = j, value yval[t]) and the user x item x word tensor X:
+ *   f = 1/2 sum_{(i,j) in Omega^Y} (y_ij - a_i . b_j)^2
+ *       + mu 1/2 ||X - [[A, B, C]]||^2 + lambda 1/2 (||A||^2 + ||B||^2 + ||C||^2)
+ * (Eq. joint-obj-fn; the tensor term runs over every cell, as in Eq. gd-obj-fn).
+ */
+double orc_joint_loss(int64_t nnzY, const int32_t* yidx, const float* yval, int64_t nnz,
+                      const int32_t* idx, const float* val, const int32_t* dims, int R, double mu,
+                      double lambda, const double* A, const double* B, const double* C) {
+  double fy = 0.0;
+  for (int64_t t = 0; t < nnzY; ++t) {
+    const int64_t i = yidx[t], j = yidx[nnzY + t];
+    double p = 0.0;
+    for (int r = 0; r < R; ++r) p += A[i * R + r] * B[j * R + r];
+    const double e = (double)yval[t] - p;
+    fy += 0.5 * e * e;
+  }
+  const double ft = orc_loss(nnz, idx, val, dims, R, 0.0, A, B, C);
+  return fy + mu * ft +
+         0.5 * lambda * (frob2(dims[0], R, A) + frob2(dims[1], R, B) + frob2(dims[2], R, C));
+}
+
+/*
+ * Row system of one factor row (Eq. grad-joint-A and the ALS solution below
+ * it).  For the user factor (side 0) and row i:
+ *   rhs = sum_{j in Omega_i} y_ij b_j + mu N_A[i]          (y_i,: B + mu x^1_i,: (C kr B))
+ *   H   = sum_{j in Omega_i} b_j^T b_j + mu (C^T C * B^T B) + lambda I
+ * where Omega_i are the observed items of user i (the printed sum over Omega^Y
+ * is read as the one over the row, the derivative of Eq. joint-prob-A).  The
+ * item factor (side 1) swaps the roles of A and B (Omega_j, N_B, A^T A * C^T C);
+ * the word factor (side 2) has no ratings: rhs = mu N_C[k], H = mu (B^T B *
+ * A^T A) + lambda I.  N is the mode's MTTKRP, Gam its Gram-Hadamard product.
+ */
+static void joint_row_system(int side, int64_t row, int64_t nnzY, const int32_t* yidx,
+                             const float* yval, int R, double mu, double lambda,
+                             const double* other, const double* N, const double* Gam,
+                             double* rhs, double* H) {
+  for (int r = 0; r < R; ++r) {
+    rhs[r] = mu * N[row * R + r];
+    for (int s = 0; s < R; ++s) H[r * R + s] = mu * Gam[r * R + s] + (r == s ? lambda : 0.0);
+  }
+  if (side == 2) return;
+  for (int64_t t = 0; t < nnzY; ++t) {
+    if (yidx[(int64_t)side * nnzY + t] != row) continue;
+    const int64_t o = yidx[(int64_t)(1 - side) * nnzY + t];
+    const double y = (double)yval[t];
+    for (int r = 0; r < R; ++r) {
+      rhs[r] += y * other[o * R + r];
+      for (int s = 0; s < R; ++s) H[r * R + s] += other[o * R + r] * other[o * R + s];
+    }
+  }
+}
+
+/* Gram-Hadamard product of the two factors that are not `side` (mode n = side). */
+static int joint_gamma(int side, const int32_t* dims, int R, const double* const* F, double* Gam) {
+  double* Gf = (double*)malloc(sizeof(double) * (size_t)R * R);
+  double* Gi = (double*)malloc(sizeof(double) * (size_t)R * R);
+  if (!Gf || !Gi) { free(Gf); free(Gi); return ORC_ENOMEM; }
+  orc_gram(dims[ax_f(side)], R, F[ax_f(side)], Gf);
+  orc_gram(dims[ax_in(side)], R, F[ax_in(side)], Gi);
+  for (int e = 0; e < R * R; ++e) Gam[e] = Gf[e] * Gi[e];
+  free(Gf);
+  free(Gi);
+  return ORC_OK;
+}
+
+/*
+ * Gradients at the current point, every row by Eq. grad-joint-A:
+ *   grad_i = -rhs_i + a_i H_i  (side 0), the same for B (side 1) and C (side 2).
+ */
+int orc_joint_gradient(int64_t nnzY, const int32_t* yidx, const float* yval, int64_t nnz,
+                       const int32_t* idx, const float* val, const int32_t* dims, int R, double mu,
+                       double lambda, const double* A, const double* B, const double* C,
+                       double* GA, double* GB, double* GC) {
+  const double* F[3] = {A, B, C};
+  double* Gout[3] = {GA, GB, GC};
+  double* N = NULL;
+  double* Gam = (double*)malloc(sizeof(double) * (size_t)R * R);
+  double* H = (double*)malloc(sizeof(double) * (size_t)R * R);
+  double* rhs = (double*)malloc(sizeof(double) * (size_t)R);
+  if (!Gam || !H || !rhs) return ORC_ENOMEM;
+  for (int side = 0; side < 3; ++side) {
+    N = (double*)malloc(sizeof(double) * (size_t)dims[side] * R);
+    if (!N) return ORC_ENOMEM;
+    orc_mttkrp(side, nnz, idx, val, dims, R, A, B, C, N);
+    joint_gamma(side, dims, R, F, Gam);
+    const double* other = side == 0 ? B : A;
+    for (int64_t row = 0; row < dims[side]; ++row) {
+      joint_row_system(side, row, nnzY, yidx, yval, R, mu, lambda, other, N, Gam, rhs, H);
+      for (int s = 0; s < R; ++s) {
+        double v = -rhs[s];
+        for (int r = 0; r < R; ++r) v += F[side][row * R + r] * H[r * R + s];
+        Gout[side][row * R + s] = v;
+      }
+    }
+    free(N);
+  }
+  free(Gam);
+  free(H);
+  free(rhs);
+  return ORC_OK;
+}
+
+/*
+ * One ALS sweep of the joint model: A row by row (a_i = rhs_i H_i^-1, the
+ * closed form of Appendix F), then B with the new A, then C with the new A and
+ * B.  H_i is symmetric positive definite when lambda > 0; the solve is the
+ * oracle's Cholesky solve (pseudo-inverse when it fails, status ORC_ESINGULAR).
+ */
+int orc_joint_als_sweep(int64_t nnzY, const int32_t* yidx, const float* yval, int64_t nnz,
+                        const int32_t* idx, const float* val, const int32_t* dims, int R,
+                        double mu, double lambda, double* A, double* B, double* C) {
+  double* F[3] = {A, B, C};
+  double* Gam = (double*)malloc(sizeof(double) * (size_t)R * R);
+  double* H = (double*)malloc(sizeof(double) * (size_t)R * R);
+  double* rhs = (double*)malloc(sizeof(double) * (size_t)R);
+  if (!Gam || !H || !rhs) return ORC_ENOMEM;
+  int status = ORC_OK;
+  for (int side = 0; side < 3; ++side) {
+    double* N = (double*)malloc(sizeof(double) * (size_t)dims[side] * R);
+    if (!N) return ORC_ENOMEM;
+    orc_mttkrp(side, nnz, idx, val, dims, R, A, B, C, N);
+    joint_gamma(side, dims, R, (const double* const*)F, Gam);
+    const double* other = side == 0 ? B : A;
+    for (int64_t row = 0; row < dims[side]; ++row) {
+      joint_row_system(side, row, nnzY, yidx, yval, R, mu, lambda, other, N, Gam, rhs, H);
+      const int st = orc_solve_normal(1, R, H, rhs, F[side] + row * R);
+      if (st == ORC_ESINGULAR) status = ORC_ESINGULAR;
+      else if (st != ORC_OK) return st;
+    }
+    free(N);
+  }
+  free(Gam);
+  free(H);
+  free(rhs);
+  return status;
+}
+
+/*
+ * One GD step of the joint model: the three gradients at the current point,
+ * then the backtracking rule of orc_gd_step on f of Eq. joint-obj-fn (the
+ * paper used backtracking for the joint model), then the update.
+ */
+int orc_joint_gd_step(int64_t nnzY, const int32_t* yidx, const float* yval, int64_t nnz,
+                      const int32_t* idx, const float* val, const int32_t* dims, int R, double mu,
+                      double lambda, double* A, double* B, double* C, double* alpha_io,
+                      double* loss_out, double* g2_out) {
+  double* F[3] = {A, B, C};
+  double* G[3];
+  double* T[3];
+  for (int m = 0; m < 3; ++m) {
+    G[m] = (double*)malloc(sizeof(double) * (size_t)dims[m] * R);
+    T[m] = (double*)malloc(sizeof(double) * (size_t)dims[m] * R);
+    if (!G[m] || !T[m]) return ORC_ENOMEM;
+  }
+  int st = orc_joint_gradient(nnzY, yidx, yval, nnz, idx, val, dims, R, mu, lambda, A, B, C, G[0],
+                              G[1], G[2]);
+  if (st != ORC_OK) return st;
+  double g2 = 0.0;
+  for (int m = 0; m < 3; ++m) g2 += frob2(dims[m], R, G[m]);
+  const double f0 = orc_joint_loss(nnzY, yidx, yval, nnz, idx, val, dims, R, mu, lambda, A, B, C);
+  double alpha = (*alpha_io > 0.0) ? fmin(2.0 * (*alpha_io), 1.0) : 1.0;
+  int accepted = 0;
+  double fa = f0;
+  for (int trial = 0; trial < 100; ++trial) {
+    for (int m = 0; m < 3; ++m)
+      for (int64_t t = 0; t < (int64_t)dims[m] * R; ++t) T[m][t] = F[m][t] - alpha * G[m][t];
+    fa = orc_joint_loss(nnzY, yidx, yval, nnz, idx, val, dims, R, mu, lambda, T[0], T[1], T[2]);
+    if (fa <= f0 - 1e-4 * alpha * g2) {
+      accepted = 1;
+      break;
+    }
+    alpha *= 0.5;
+  }
+  if (g2_out) *g2_out = g2;
+  st = ORC_OK;
+  if (accepted) {
+    for (int m = 0; m < 3; ++m) memcpy(F[m], T[m], sizeof(double) * (size_t)dims[m] * R);
+    *alpha_io = alpha;
+    if (loss_out) *loss_out = fa;
+  } else {
+    st = ORC_ELSFAIL;
+    if (loss_out) *loss_out = f0;
+  }
+  for (int m = 0; m < 3; ++m) {
+    free(G[m]);
+    free(T[m]);
+  }
+  return st;
+}

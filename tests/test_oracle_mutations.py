@@ -49,6 +49,11 @@ MUTATIONS = {
     "ray_gram_cross_term_halved": ("M[n][R * R + r * R + s] -= fr * gs + gr * fs;",
                                    "M[n][R * R + r * R + s] -= fr * gs;"),
     "ray_ridge_slope_dropped": ("        coef[1] -= lambda_reg * F[n][t] * G[n][t];\n", "\n"),
+    "joint_row_gram_dropped": ("      for (int s = 0; s < R; ++s) H[r * R + s] += other[o * R + r] * other[o * R + s];",
+                               "      (void)0;"),
+    "joint_rating_side_swapped": ("    const int64_t o = yidx[(int64_t)(1 - side) * nnzY + t];",
+                                  "    const int64_t o = yidx[(int64_t)side * nnzY + t];"),
+    "joint_tensor_term_unweighted": ("    rhs[r] = mu * N[row * R + r];", "    rhs[r] = N[row * R + r];"),
 }
 
 

@@ -499,6 +499,146 @@ def test_gd_line_search_failure_leaves_factors():
 
 
 # ---------------------------------------------------------------------------
+# Joint matrix completion and tensor factorization (Appendix F).
+# ---------------------------------------------------------------------------
+
+
+def joint_problem(seed, dims=(7, 6, 5), R=3, density=0.35, ny=20):
+    rng = np.random.default_rng(seed)
+    t = random_sparse(rng, list(dims), density)
+    lin = rng.choice(dims[0] * dims[1], size=ny, replace=False)
+    yi, yj = np.divmod(lin, dims[1])
+    y = oracle.Ratings(np.stack([yi, yj]), rng.uniform(0.0, 5.0, ny))
+    F = [rng.standard_normal((d, R)) for d in dims]
+    return rng, t, y, F
+
+
+def dense_joint_loss(X, Ymask, Y, F, mu, lam):
+    """Eq. joint-obj-fn from dense arrays: the observed ratings (Ymask), every
+    cell of X, and the ridge."""
+    A, B, C = F
+    fy = 0.5 * float(np.sum(Ymask * (Y - A @ B.T) ** 2))
+    return fy + mu * dense_loss(X, F, 0.0) + 0.5 * lam * sum(float(np.sum(f * f)) for f in F)
+
+
+def dense_ratings(y, dims):
+    Ymask = np.zeros((dims[0], dims[1]))
+    Y = np.zeros((dims[0], dims[1]))
+    Ymask[y.idx[0], y.idx[1]] = 1.0
+    Y[y.idx[0], y.idx[1]] = y.val
+    return Ymask, Y
+
+
+@pytest.mark.parametrize("mu,lam", [(1.0, 0.0), (0.3, 0.5), (0.0, 0.2)])
+def test_joint_loss_and_gradient(mu, lam):
+    """The joint objective equals its dense definition, and its gradient (Eq.
+    grad-joint-A for every row of A, B and C) equals central finite differences
+    of the dense objective."""
+    rng, t, y, F = joint_problem(51)
+    dims = list(t.dims)
+    X = dense_from_coo(t.idx, t.val, dims)
+    Ymask, Y = dense_ratings(y, dims)
+    assert oracle.joint_loss(y, t, F, mu, lam) == pytest.approx(
+        dense_joint_loss(X, Ymask, Y, F, mu, lam), rel=1e-12)
+    G = oracle.joint_gradient(y, t, F, mu, lam)
+    h = 1e-6
+    for m in range(3):
+        fd = np.zeros_like(F[m])
+        for i in range(F[m].shape[0]):
+            for r in range(F[m].shape[1]):
+                Fp = [f.copy() for f in F]
+                Fm = [f.copy() for f in F]
+                Fp[m][i, r] += h
+                Fm[m][i, r] -= h
+                fd[i, r] = (dense_joint_loss(X, Ymask, Y, Fp, mu, lam)
+                            - dense_joint_loss(X, Ymask, Y, Fm, mu, lam)) / (2 * h)
+        np.testing.assert_allclose(G[m], fd, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("mu,lam", [(1.0, 0.1), (0.05, 1.0)])
+def test_joint_als_rows_are_ridge_least_squares(mu, lam):
+    """Each row update of the joint ALS sweep (A, then B with the new A, then C
+    with the new A and B) is the minimiser of the joint objective over that row:
+    a ridge least-squares problem whose design stacks the row's ratings, every
+    cell of the tensor's matching slice (weight sqrt(mu)) and sqrt(lambda) I,
+    solved here by numpy's lstsq."""
+    rng, t, y, F = joint_problem(52)
+    dims = list(t.dims)
+    R = F[0].shape[1]
+    X = dense_from_coo(t.idx, t.val, dims)
+    Ymask, Y = dense_ratings(y, dims)
+    st, Fs = oracle.joint_als_sweep(y, t, F, mu, lam)
+    assert st == oracle.OK
+    cur = [f.copy() for f in F]
+    for side in range(3):
+        want = np.zeros_like(F[side])
+        for row in range(dims[side]):
+            rows, rhs = [], []
+            if side < 2:
+                other = cur[1 - side]
+                obs = np.nonzero(Ymask[row] if side == 0 else Ymask[:, row])[0]
+                for o in obs:
+                    rows.append(other[o])
+                    rhs.append(Y[row, o] if side == 0 else Y[o, row])
+            # tensor slice: x[row, :, :] against the Khatri-Rao rows of the other two
+            o1, o2 = [m for m in range(3) if m != side]
+            sl = np.take(X, row, axis=side)  # dims[o1] x dims[o2]
+            for p in range(dims[o1]):
+                for q in range(dims[o2]):
+                    rows.append(np.sqrt(mu) * cur[o1][p] * cur[o2][q])
+                    rhs.append(np.sqrt(mu) * sl[p, q])
+            for r in range(R):
+                e = np.zeros(R)
+                e[r] = np.sqrt(lam)
+                rows.append(e)
+                rhs.append(0.0)
+            want[row] = np.linalg.lstsq(np.array(rows), np.array(rhs), rcond=None)[0]
+        np.testing.assert_allclose(Fs[side], want, rtol=1e-9, atol=1e-10)
+        cur[side] = want
+
+
+def test_joint_als_sweeps_decrease_the_objective():
+    """Every block update minimises the objective exactly, so the joint
+    objective never increases over ALS sweeps."""
+    rng, t, y, F = joint_problem(53, dims=(9, 8, 6), density=0.3, ny=30)
+    prev = oracle.joint_loss(y, t, F, 0.7, 0.2)
+    for _ in range(6):
+        st, F = oracle.joint_als_sweep(y, t, F, 0.7, 0.2)
+        assert st == oracle.OK
+        cur = oracle.joint_loss(y, t, F, 0.7, 0.2)
+        assert cur <= prev * (1 + 1e-12)
+        prev = cur
+
+
+def test_joint_gd_step_is_backtracking_on_the_joint_objective():
+    """Each joint GD step reproduces an independent backtracking run on the
+    dense joint objective (the rule of the tensor GD step)."""
+    rng, t, y, F = joint_problem(54)
+    dims = list(t.dims)
+    X = dense_from_coo(t.idx, t.val, dims)
+    Ymask, Y = dense_ratings(y, dims)
+    mu, lam = 0.5, 0.1
+    alpha = 0.0
+    prev = dense_joint_loss(X, Ymask, Y, F, mu, lam)
+    for it in range(6):
+        G = oracle.joint_gradient(y, t, F, mu, lam)
+        g2 = sum(float(np.sum(g * g)) for g in G)
+        a = 1.0 if alpha <= 0 else min(2 * alpha, 1.0)
+        for _ in range(100):
+            if dense_joint_loss(X, Ymask, Y, [f - a * g for f, g in zip(F, G)], mu, lam) <= prev - 1e-4 * a * g2:
+                break
+            a *= 0.5
+        st, F2, alpha, lo, g2o = oracle.joint_gd_step(y, t, F, mu, lam, alpha)
+        assert st == oracle.OK
+        assert alpha == a
+        assert g2o == pytest.approx(g2, rel=1e-12)
+        for m in range(3):
+            np.testing.assert_allclose(F2[m], F[m] - alpha * G[m], rtol=1e-14, atol=1e-14)
+        assert lo == pytest.approx(dense_joint_loss(X, Ymask, Y, F2, mu, lam), rel=1e-12)
+        F, prev = F2, lo
+
+
+# ---------------------------------------------------------------------------
 # Error paths.
 # ---------------------------------------------------------------------------
 
