@@ -307,6 +307,74 @@ dfacto_status dfacto_mttkrp_noalloc(const dfacto_csr_view* csr, const float* F_i
                                     int32_t R, float* out, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Joint matrix completion and tensor factorization (Appendix F).
+ *
+ * A ratings matrix Y (users x items, dims[0] x dims[1], observed entries
+ * Omega^Y) and the handle's user x item x word tensor X share the user factor
+ * A and the item factor B (Eq. joint-obj-fn):
+ *   f = 1/2 sum_{(i,j) in Omega^Y} (y_ij - a_i . b_j)^2
+ *       + mu 1/2 ||X - [[A, B, C]]||^2 + lambda 1/2 (||A||^2 + ||B||^2 + ||C||^2)
+ * with lambda the handle's lambda_reg.  The model has no CP weights (they
+ * are kept at 1) and needs R <= 32.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * dfacto_joint_set_ratings -- attach the ratings to a built handle (replacing
+ * earlier ones) and build their two CSR copies on the device (by user and by
+ * item, columns ascending within a row).
+ *   yidx  int32[2][nnzY], structure of arrays: yidx[t] is the user (row of A,
+ *         < dims[0]) and yidx[nnzY + t] the item (row of B, < dims[1]) of
+ *         rating t.  Host or device; the caller keeps ownership.
+ *   yval  float[nnzY], host or device.
+ *   nnzY  0 <= nnzY <= 2^31 - 2^16.
+ *   mu    weight of the tensor term, >= 0.
+ * Errors: EINVAL (bad arguments, R > 32, handle in a batch), ERANGE (a rating
+ * outside dims[0] x dims[1]), EDUP (two ratings of one (user, item)), ENOMEM,
+ * ECUDA.  Synchronizes.
+ */
+dfacto_status dfacto_joint_set_ratings(dfacto_t* h, const int32_t* yidx, const float* yval,
+                                       int64_t nnzY, double mu);
+
+/* Device pointers to one CSR copy of the ratings: side 0 rows are users
+ * (col = item), side 1 rows are items (col = user); ptr[rows + 1]. */
+typedef struct dfacto_ratings_view {
+  int64_t rows;
+  int64_t nnz;
+  const int64_t* ptr;
+  const int32_t* col;
+  const float* val;
+} dfacto_ratings_view;
+dfacto_status dfacto_get_ratings_csr(dfacto_t* h, int side, dfacto_ratings_view* view);
+
+/*
+ * dfacto_joint_als_iter -- one ALS sweep of the joint model: every row of A by
+ * the closed form of Appendix F,
+ *   a_i = [sum_{j in Omega_i} y_ij b_j + mu N_A[i]]
+ *         [sum_{j in Omega_i} b_j^T b_j + mu C^T C * B^T B + lambda I]^-1
+ * (N_A = X^1 (C kr B), the MTTKRP of Algorithm 1; the sum in the bracket runs
+ * over the user's own ratings), then B the same way with the new A, then C
+ * (tensor term only).  One R x R Cholesky solve per row in FP64; needs
+ * lambda_reg > 0 (EINVAL otherwise), which makes every system positive
+ * definite.
+ *   obj_out  host double, nullable: f after the sweep (synchronizes).
+ */
+dfacto_status dfacto_joint_als_iter(dfacto_t* h, double* obj_out);
+
+/*
+ * dfacto_joint_gd_iter -- one GD step of the joint model: the gradients of
+ * Eq. grad-joint-A for A, B and C at the current point, then the step size by
+ * the handle's line_search option (backtracking as dfacto_gd_iter, or the
+ * exact minimiser: along the ray f is a polynomial of degree 6, its ratings
+ * term a quartic from one pass over the ratings), then the update.
+ *   obj_out, alpha_out  host doubles, nullable (both NULL: no synchronization).
+ * Returns DFACTO_ELSFAIL (factors unchanged) when no step is accepted.
+ */
+dfacto_status dfacto_joint_gd_iter(dfacto_t* h, double* obj_out, double* alpha_out);
+
+/* f of the joint model at the current factors (synchronizes). */
+dfacto_status dfacto_joint_objective(dfacto_t* h, double* obj_out);
+
+/* ------------------------------------------------------------------------
  * Batches: many independent decompositions advanced together.
  *
  * The paper factorizes one tensor at a time; a batch runs the ALS sweep of

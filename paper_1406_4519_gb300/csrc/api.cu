@@ -232,6 +232,7 @@ const char* dfacto_status_str(dfacto_status s) {
 void dfacto_destroy(dfacto_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  joint_free(h);
   if (h->batch) {  // the factors belong to the batch's pools
     batch_forget(h->batch, h);
     for (int m = 0; m < 3; ++m) h->F[m] = nullptr;

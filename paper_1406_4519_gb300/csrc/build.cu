@@ -366,6 +366,11 @@ cudaError_t radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, i
 
 }  // namespace
 
+cudaError_t sort_pairs64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
+                         int lo_bit, int hi_bit, cudaStream_t s, bool* in_alt) {
+  return radix_sort(k0, v0, k1, v1, n, lo_bit, hi_bit, s, in_alt);
+}
+
 cudaError_t launch_segment_starts(const int64_t* nz_ptr, int64_t nfib, int64_t nseg, int64_t seg,
                                   int32_t* seg_fib, cudaStream_t s) {
   if (nseg <= 0) return cudaSuccess;

@@ -839,9 +839,12 @@ __device__ int poly_roots(const double* c, int n, double lo, double hi, double* 
 // evaluated in the factored form above, and the smallest is taken when it
 // lowers f; when there is none (possible only through rounding of a
 // degenerate ray), the step falls back to backtracking.
+// The joint model of Appendix F weights the tensor term by mu and adds the
+// ratings term, a quartic in alpha with coefficients ycoef[0..4] (nullable).
 __global__ void __launch_bounds__(256) gd_line_search(const double* __restrict__ mats, int R,
                                                      double lambda_reg, double* __restrict__ scal,
-                                                     int32_t* __restrict__ lsfail, int exact) {
+                                                     int32_t* __restrict__ lsfail, int exact,
+                                                     double mu, const double* __restrict__ ycoef) {
   __shared__ double red[256];
   __shared__ double s_q;
   __shared__ double s_qc[256][7];
@@ -887,8 +890,9 @@ __global__ void __launch_bounds__(256) gd_line_search(const double* __restrict__
   const double t3 = scal[kT111];
   auto f = [&](double a) {
     const double P = t0 - a * t1 + a * a * t2 - a * a * a * t3;
-    double v = 0.5 * (nx2 - 2.0 * P + Q(a));
+    double v = 0.5 * mu * (nx2 - 2.0 * P + Q(a));
     if (lambda_reg != 0.0) v += 0.5 * lambda_reg * trace_sum(a);
+    if (ycoef) v += ycoef[0] + a * (ycoef[1] + a * (ycoef[2] + a * (ycoef[3] + a * ycoef[4])));
     return v;
   };
   const double f0 = f(0.0);
@@ -928,13 +932,15 @@ __global__ void __launch_bounds__(256) gd_line_search(const double* __restrict__
         }
       }
       double c[7];
-      c[0] = 0.5 * (nx2 - 2.0 * t0 + qc[0]) + 0.5 * lambda_reg * tr[0];
-      c[1] = 0.5 * (2.0 * t1 + qc[1]) - 0.5 * lambda_reg * tr[1];
-      c[2] = 0.5 * (-2.0 * t2 + qc[2]) + 0.5 * lambda_reg * tr[2];
-      c[3] = 0.5 * (2.0 * t3 + qc[3]);
-      c[4] = 0.5 * qc[4];
-      c[5] = 0.5 * qc[5];
-      c[6] = 0.5 * qc[6];
+      c[0] = 0.5 * mu * (nx2 - 2.0 * t0 + qc[0]) + 0.5 * lambda_reg * tr[0];
+      c[1] = 0.5 * mu * (2.0 * t1 + qc[1]) - 0.5 * lambda_reg * tr[1];
+      c[2] = 0.5 * mu * (-2.0 * t2 + qc[2]) + 0.5 * lambda_reg * tr[2];
+      c[3] = 0.5 * mu * (2.0 * t3 + qc[3]);
+      c[4] = 0.5 * mu * qc[4];
+      c[5] = 0.5 * mu * qc[5];
+      c[6] = 0.5 * mu * qc[6];
+      if (ycoef)
+        for (int k = 0; k < 5; ++k) c[k] += ycoef[k];
       double d[kPolyMax + 1];
       for (int k = 0; k <= kPolyMax; ++k) d[k] = (double)(k + 1) * c[k + 1];
       int n = kPolyMax;
@@ -1959,7 +1965,7 @@ dfacto_status gd_step_rows(dfacto_t* h) {
   }
   if ((st = dual_pass(h)) != DFACTO_OK) return st;
   gd_line_search<<<1, 256, 0, s>>>(h->gd_mats, R, h->lambda_reg, h->scal, h->flags + kFlagLsFail,
-                                   h->opt.line_search);
+                                   h->opt.line_search, 1.0, nullptr);
   DF_COUNT();
   for (int m = 0; m < 3; ++m) {
     const int64_t rows = h->dims[m];
@@ -2017,7 +2023,7 @@ dfacto_status gd_step_T(dfacto_t* h) {
   }
   if ((st = dual_pass(h)) != DFACTO_OK) return st;
   gd_line_search<<<1, 256, 0, s>>>(h->gd_mats, R, h->lambda_reg, h->scal, h->flags + kFlagLsFail,
-                                   h->opt.line_search);
+                                   h->opt.line_search, 1.0, nullptr);
   DF_COUNT();
   for (int m = 0; m < 3; ++m) {
     const int64_t n = (int64_t)h->dims[m] * R;
@@ -2036,6 +2042,57 @@ dfacto_status gd_step_T(dfacto_t* h) {
 
 dfacto_status gd_step(dfacto_t* h) {
   return h->dtype == DFACTO_BF16 ? gd_step_T<__nv_bfloat16>(h) : gd_step_T<float>(h);
+}
+
+namespace {
+template <typename T>
+dfacto_status ray_matrices_T(dfacto_t* h) {
+  const int R = h->R;
+  cudaStream_t s = h->stream;
+  dfacto_status st;
+  for (int m = 0; m < 3; ++m) {
+    if (!h->gram_valid[m] && (st = gram_of_factor(h, m)) != DFACTO_OK) return st;
+    double* P = h->gd_mats + (size_t)m * 3 * R * R;
+    DF_CUDA(h, cudaMemcpyAsync(P, h->gram[m], sizeof(double) * R * R, cudaMemcpyDeviceToDevice, s));
+    if ((st = cross_gram<T, float, false>(h, static_cast<const T*>(h->F[m]), h->grad[m], h->dims[m],
+                                          P + R * R, true)) != DFACTO_OK)
+      return st;
+    if ((st = cross_gram<float, float, true>(h, h->grad[m], h->grad[m], h->dims[m], P + 2 * R * R,
+                                             false)) != DFACTO_OK)
+      return st;
+  }
+  return DFACTO_OK;
+}
+
+template <typename T>
+dfacto_status apply_step_T(dfacto_t* h) {
+  const int R = h->R;
+  for (int m = 0; m < 3; ++m) {
+    const int64_t n = (int64_t)h->dims[m] * R;
+    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, kMaxBlocks * 4));
+    gd_update<T><<<nb, 256, 0, h->stream>>>(static_cast<T*>(h->F[m]), h->grad[m], n, h->scal);
+    DF_COUNT();
+    h->gram_valid[m] = false;
+  }
+  DF_CUDA(h, cudaGetLastError());
+  return DFACTO_OK;
+}
+}  // namespace
+
+dfacto_status ray_matrices(dfacto_t* h) {
+  return h->dtype == DFACTO_BF16 ? ray_matrices_T<__nv_bfloat16>(h) : ray_matrices_T<float>(h);
+}
+
+dfacto_status line_search(dfacto_t* h, double mu, const double* ycoef) {
+  gd_line_search<<<1, 256, 0, h->stream>>>(h->gd_mats, h->R, h->lambda_reg, h->scal,
+                                           h->flags + kFlagLsFail, h->opt.line_search, mu, ycoef);
+  DF_COUNT();
+  DF_CUDA(h, cudaGetLastError());
+  return DFACTO_OK;
+}
+
+dfacto_status apply_step(dfacto_t* h) {
+  return h->dtype == DFACTO_BF16 ? apply_step_T<__nv_bfloat16>(h) : apply_step_T<float>(h);
 }
 
 cudaError_t batch_gamma_inverse(const DenseJob* jobs, int n, int R, cudaStream_t s) {

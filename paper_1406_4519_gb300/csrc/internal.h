@@ -12,6 +12,8 @@
 
 namespace dfacto {
 
+struct JointState;  // joint.cu
+
 // Lane-group configuration of the MTTKRP walk: each group of G lanes owns one
 // segment of the nonzero stream and each lane owns VEC consecutive columns.
 struct WalkCfg {
@@ -117,6 +119,8 @@ struct dfacto_handle {
   // Set while the handle is in a batch: F[m] then point into the batch's
   // factor pools and are not the handle's to free.
   dfacto_batch* batch = nullptr;
+  // Ratings of the joint model (Appendix F), set by dfacto_joint_set_ratings.
+  dfacto::JointState* joint = nullptr;
 };
 
 namespace dfacto {
@@ -153,6 +157,10 @@ cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaS
 
 // ---- build (build.cu) -----------------------------------------------------
 dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val);
+// Stable LSD radix sort of (key, payload) pairs by key bits [lo_bit, hi_bit);
+// the result is in (k0, v0), or in (k1, v1) when *in_alt is set.
+cudaError_t sort_pairs64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
+                         int lo_bit, int hi_bit, cudaStream_t s, bool* in_alt);
 dfacto_status ensure_segments(dfacto_t* h, int mode);
 
 // ---- MTTKRP (mttkrp*.cu) --------------------------------------------------
@@ -198,6 +206,9 @@ cudaError_t batch_fit(const DenseJob* jobs, int n, int R, cudaStream_t s);
 // Called by dfacto_destroy for a handle still in a batch: the batch drops it.
 void batch_forget(dfacto_batch* b, dfacto_t* h);
 
+// Frees the joint model's ratings and buffers (joint.cu); called by dfacto_destroy.
+void joint_free(dfacto_t* h);
+
 // ---- dense R x R and row-wise kernels (dense.cu) --------------------------
 dfacto_status gram_of_factor(dfacto_t* h, int m);
 dfacto_status als_mode(dfacto_t* h, int mode);
@@ -209,5 +220,13 @@ dfacto_status gd_step(dfacto_t* h);
 dfacto_status convert_factor_in(dfacto_t* h, int m, const void* src, int src_dtype);
 dfacto_status convert_factor_out(dfacto_t* h, int m, void* dst, int dst_dtype);
 dfacto_status norm_x2(dfacto_t* h);
+// GD pieces shared with the joint model (joint.cu): the R x R matrices of the
+// search ray (P0, P1, P2 per factor from h->F and h->grad), the line search
+// on the ray (tensor term weighted by mu, plus the ratings quartic ycoef[0..4]
+// when non-null; step into scal[kStep]), and theta <- theta - step grad.
+dfacto_status ray_matrices(dfacto_t* h);
+dfacto_status line_search(dfacto_t* h, double mu, const double* ycoef);
+dfacto_status apply_step(dfacto_t* h);
+dfacto_status dual_pass(dfacto_t* h);  // T110, T101, T011, T111 of the ray (dual.cu)
 
 }  // namespace dfacto

@@ -53,6 +53,11 @@ class dfacto_csr_view(ctypes.Structure):
                 ("nz_val", ctypes.c_void_p)]
 
 
+class dfacto_ratings_view(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("nnz", ctypes.c_int64), ("ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
 class dfacto_batch_options(ctypes.Structure):
     _fields_ = [("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 6)]
@@ -88,6 +93,11 @@ SIGNATURES = {
     "dfacto_fit": (_I, [_P, _P]),
     "dfacto_get_csr": (_I, [_P, _I, _P]),
     "dfacto_mttkrp_noalloc": (_I, [_P, _P, _P, ctypes.c_int32, _P, _P]),
+    "dfacto_joint_set_ratings": (_I, [_P, _P, _P, _I64, _D]),
+    "dfacto_get_ratings_csr": (_I, [_P, _I, _P]),
+    "dfacto_joint_als_iter": (_I, [_P, _P]),
+    "dfacto_joint_gd_iter": (_I, [_P, _P, _P]),
+    "dfacto_joint_objective": (_I, [_P, _P]),
     "dfacto_batch_options_init": (None, [_P]),
     "dfacto_batch_create": (_I, [_P, ctypes.c_int32, _P, _P, _P]),
     "dfacto_batch_destroy": (None, [_P]),
@@ -287,6 +297,54 @@ def dfacto_mttkrp_noalloc(csr: dfacto_csr_view, F_in: torch.Tensor, F_f: torch.T
     return out
 
 
+def dfacto_joint_set_ratings(h, yidx: torch.Tensor, yval: torch.Tensor, mu: float) -> None:
+    """yidx int32 [2, nnzY] (user, item), yval float32 [nnzY]; CPU or CUDA tensors."""
+    assert yidx.dtype == torch.int32 and yval.dtype == torch.float32
+    yidx = yidx.contiguous()
+    yval = yval.contiguous()
+    n = int(yval.numel())
+    assert yidx.numel() == 2 * n
+    _check(load().dfacto_joint_set_ratings(h, yidx.data_ptr() if n else None,
+                                           yval.data_ptr() if n else None, n, float(mu)), h)
+
+
+def dfacto_get_ratings_csr(h, side: int) -> dfacto_ratings_view:
+    v = dfacto_ratings_view()
+    _check(load().dfacto_get_ratings_csr(h, int(side), ctypes.byref(v)), h)
+    return v
+
+
+def dfacto_joint_als_iter(h, want: bool = True) -> Optional[float]:
+    obj = ctypes.c_double(0.0)
+    _check(load().dfacto_joint_als_iter(h, ctypes.byref(obj) if want else None), h)
+    return obj.value if want else None
+
+
+def dfacto_joint_gd_iter(h, want: bool = True) -> Tuple[int, Optional[float], Optional[float]]:
+    obj = ctypes.c_double(0.0)
+    alpha = ctypes.c_double(0.0)
+    if want:
+        st = load().dfacto_joint_gd_iter(h, ctypes.byref(obj), ctypes.byref(alpha))
+    else:
+        st = load().dfacto_joint_gd_iter(h, None, None)
+    st = _check(st, h, allow=(ELSFAIL,))
+    return st, (obj.value if want else None), (alpha.value if want else None)
+
+
+def dfacto_joint_objective(h) -> float:
+    obj = ctypes.c_double(0.0)
+    _check(load().dfacto_joint_objective(h, ctypes.byref(obj)), h)
+    return obj.value
+
+
+def ratings_to_tensors(view: dfacto_ratings_view) -> dict:
+    """Copies (torch tensors on the GPU) of the arrays of a ratings CSR view."""
+    torch.cuda.synchronize()
+    return dict(ptr=device_view(view.ptr, view.rows + 1, torch.int64).clone(),
+                col=device_view(view.col, view.nnz, torch.int32).clone(),
+                val=device_view(view.val, view.nnz, torch.float32).clone())
+
+
 def csr_to_tensors(view: dfacto_csr_view) -> dict:
     """Copies (torch tensors on the GPU) of the arrays of a CSR view."""
     torch.cuda.synchronize()
@@ -319,6 +377,19 @@ class Tensor:
     def set_factors(self, factors) -> None:
         for m, F in enumerate(factors):
             dfacto_set_factors(self.h, m, F)
+
+    # joint matrix completion + tensor factorization (Appendix F)
+    def set_ratings(self, yidx, yval, mu: float) -> None:
+        dfacto_joint_set_ratings(self.h, yidx, yval, mu)
+
+    def joint_als_iter(self, want: bool = True):
+        return dfacto_joint_als_iter(self.h, want)
+
+    def joint_gd_iter(self, want: bool = True):
+        return dfacto_joint_gd_iter(self.h, want)
+
+    def joint_objective(self) -> float:
+        return dfacto_joint_objective(self.h)
 
     def factors(self, dtype=torch.float32, device="cuda"):
         return [dfacto_get_factors(self.h, m, torch.empty(d, self.rank, dtype=dtype, device=device))

@@ -18,6 +18,9 @@ measured on; the paper's real datasets are not available, these stand in):
   another, each axis index with probability proportional to (1 + the number of
   nonzeros already at that index), values U(0,1).
 * ``normal_factors``  -- N(0,1) starting factors.
+* ``joint_ratings_reviews`` -- the joint model's inputs (Appendix F): a users x
+  items ratings matrix and a users x items x words review tensor on the rated
+  pairs, from planted factors.
 
 Coordinates are returned as int32 [3, nnz] (rows i, j, k), values as float32,
 in a seeded random order (never pre-sorted).
@@ -32,7 +35,7 @@ import torch
 __all__ = [
     "generator", "zipf_cdf", "draw_zipf", "unique_coords", "uniform_tensor",
     "zipf_tensor", "preferential_attachment_tensor", "normal_factors", "batch_job_specs",
-    "poisson_arrivals",
+    "poisson_arrivals", "joint_ratings_reviews",
 ]
 
 
@@ -270,3 +273,48 @@ def poisson_arrivals(n: int, rate_per_s: float, seed: int) -> List[float]:
     u = torch.rand(n, generator=g, dtype=torch.float64).clamp_(min=1e-300)
     gaps = -torch.log(u) / float(rate_per_s)
     return torch.cumsum(gaps, 0).tolist()
+
+
+def joint_ratings_reviews(users: int, items: int, words: int, n_ratings: int, words_per_review: int,
+                          R: int, seed: int, device="cpu", noise: float = 0.1):
+    """Inputs of the joint matrix completion + tensor factorization model: the
+    real review data is not available, so ratings and reviews come from planted
+    factors A (users x R), B (items x R), C (words x R) with N(0, 1/R) entries.
+
+    Rated (user, item) pairs: ``n_ratings`` unique pairs, users and items each
+    Zipf(1.1) (a few users rate a lot, a few items are rated a lot); rating
+    y = 3 + 5 a_i . b_j + N(0, noise^2).  Each rated pair carries a review of
+    ``words_per_review`` words drawn Zipf(1.2) over the vocabulary (repeats
+    dropped), with value x = sum_r a_ir b_jr c_kr + N(0, noise^2).
+
+    Returns (yidx int32 [2, n], yval float32 [n], idx int32 [3, nnz],
+    val float32 [nnz]); pairs and nonzeros in seeded random order.
+    """
+    device = torch.device(device)
+    g = generator(seed, device)
+    s = 1.0 / math.sqrt(R)
+    A = torch.randn(users, R, generator=g, device=device) * s
+    B = torch.randn(items, R, generator=g, device=device) * s
+    C = torch.randn(words, R, generator=g, device=device) * s
+    cu, ci = zipf_cdf(users, 1.1).to(device), zipf_cdf(items, 1.1).to(device)
+
+    def pair_sampler(m):
+        return torch.stack([draw_zipf(m, cu, g, device), draw_zipf(m, ci, g, device),
+                            torch.zeros(m, dtype=torch.int64, device=device)])
+
+    pairs = unique_coords([users, items, 1], n_ratings, pair_sampler, g, device)[:2]
+    pairs = pairs[:, torch.randperm(pairs.shape[1], generator=g, device=device)]
+    yval = 3.0 + 5.0 * (A[pairs[0]] * B[pairs[1]]).sum(1)
+    yval = yval + noise * torch.randn(yval.shape[0], generator=g, device=device)
+    cw = zipf_cdf(words, 1.2).to(device)
+    rep_i = pairs[0].repeat_interleave(words_per_review)
+    rep_j = pairs[1].repeat_interleave(words_per_review)
+    wk = draw_zipf(rep_i.shape[0], cw, g, device)
+    ijk = torch.stack([rep_i, rep_j, wk])
+    keep = _first_occurrences(_key_columns(ijk, [users, items, words]))
+    ijk = _shuffle(ijk[:, keep], g, device)
+    val = (A[ijk[0]] * B[ijk[1]] * C[ijk[2]]).sum(1)
+    val = val + noise * torch.randn(val.shape[0], generator=g, device=device)
+    return (pairs.to(torch.int32).contiguous(), yval.to(torch.float32).contiguous(),
+            ijk.to(torch.int32).contiguous(), val.to(torch.float32).contiguous())
+

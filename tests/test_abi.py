@@ -53,6 +53,7 @@ int main(void) {
   printf("%zu %zu %zu %zu\\n", sizeof(dfacto_info), offsetof(dfacto_info, nnz),
          offsetof(dfacto_info, norm_x2), offsetof(dfacto_info, vec));
   printf("%zu %zu\\n", sizeof(dfacto_csr_view), offsetof(dfacto_csr_view, nz_val));
+  printf("%zu %zu\\n", sizeof(dfacto_ratings_view), offsetof(dfacto_ratings_view, val));
   printf("%zu %zu\\n", sizeof(dfacto_batch_options), offsetof(dfacto_batch_options, reserved));
   printf("%zu %zu %zu\\n", sizeof(dfacto_batch_class), offsetof(dfacto_batch_class, nnz),
          offsetof(dfacto_batch_class, tuned_ms));
@@ -68,6 +69,7 @@ int main(void) {
             ctypes.sizeof(dfacto.dfacto_info), dfacto.dfacto_info.nnz.offset,
             dfacto.dfacto_info.norm_x2.offset, dfacto.dfacto_info.vec.offset,
             ctypes.sizeof(dfacto.dfacto_csr_view), dfacto.dfacto_csr_view.nz_val.offset,
+            ctypes.sizeof(dfacto.dfacto_ratings_view), dfacto.dfacto_ratings_view.val.offset,
             ctypes.sizeof(dfacto.dfacto_batch_options), dfacto.dfacto_batch_options.reserved.offset,
             ctypes.sizeof(dfacto.dfacto_batch_class), dfacto.dfacto_batch_class.nnz.offset,
             dfacto.dfacto_batch_class.tuned_ms.offset]
@@ -116,6 +118,12 @@ def test_host_side_argument_checks(lib):
                 "dfacto_fit": (None, None), "dfacto_sync": (None,)}[fn]
         assert getattr(lib, fn)(*args) == dfacto.EINVAL
     assert lib.dfacto_status_str(dfacto.EDUP) == b"duplicate coordinate"
+    # the joint model's entry points refuse a null handle
+    assert lib.dfacto_joint_set_ratings(None, None, None, 0, 1.0) == dfacto.EINVAL
+    assert lib.dfacto_joint_als_iter(None, None) == dfacto.EINVAL
+    assert lib.dfacto_joint_gd_iter(None, None, None) == dfacto.EINVAL
+    assert lib.dfacto_joint_objective(None, None) == dfacto.EINVAL
+    assert lib.dfacto_get_ratings_csr(None, 0, None) == dfacto.EINVAL
 
 
 def test_batch_host_side_argument_checks(lib):

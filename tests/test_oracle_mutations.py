@@ -33,11 +33,17 @@ MUTATIONS = {
     "gram_hadamard_uses_one_gram": ("Gf[r * R + s] *= Gi[r * R + s];",
                                     "Gf[r * R + s] *= Gf[r * R + s];"),
     "armijo_ignores_previous_step": (
-        "double alpha = (*alpha_io > 0.0) ? fmin(2.0 * (*alpha_io), 1.0) : 1.0;",
-        "double alpha = 1.0;"),
-    "backtracking_factor_wrong": ("    alpha *= 0.5;\n", "    alpha *= 0.25;\n"),
-    "gd_update_sign": ("T[m][t] = F[m][t] - alpha * G[m][t];",
-                       "T[m][t] = F[m][t] + alpha * G[m][t];"),
+        "lambda_reg, A, B, C);\n  double alpha = (*alpha_io > 0.0) ? fmin(2.0 * (*alpha_io), 1.0) : 1.0;",
+        "lambda_reg, A, B, C);\n  double alpha = 1.0;"),
+    "backtracking_factor_wrong": ("    alpha *= 0.5;\n  }\n  if (g2_out) *g2_out = g2;\n  int st",
+                                  "    alpha *= 0.25;\n  }\n  if (g2_out) *g2_out = g2;\n  int st"),
+    "gd_update_sign": ("T[m][t] = F[m][t] - alpha * G[m][t];\n    fa = orc_loss(",
+                       "T[m][t] = F[m][t] + alpha * G[m][t];\n    fa = orc_loss("),
+    "joint_armijo_ignores_previous_step": (
+        "lambda, A, B, C);\n  double alpha = (*alpha_io > 0.0) ? fmin(2.0 * (*alpha_io), 1.0) : 1.0;",
+        "lambda, A, B, C);\n  double alpha = 1.0;"),
+    "joint_update_sign": ("T[m][t] = F[m][t] - alpha * G[m][t];\n    fa = orc_joint_loss(",
+                          "T[m][t] = F[m][t] + alpha * G[m][t];\n    fa = orc_joint_loss("),
     "normalisation_inverted": ("for (int64_t i = 0; i < n; ++i) F[o][i * R + r] /= s;",
                                "for (int64_t i = 0; i < n; ++i) F[o][i * R + r] *= s;"),
     "backsubstitution_transposed": ("for (int k = r + 1; k < R; ++k) s -= L[k * R + r] * X[i * R + k];",
