@@ -551,6 +551,27 @@ def run_ours(args, rank, world, local_rank):
     st_gd, loss, alpha = tg.gd_iter(want=True)
     del tg
 
+    # -- GD with each step-size rule from the same start: objective after each
+    # of the first steps (untimed), then the exact rule's step time ---------------
+    def gd_trace(rule, n):
+        th = dfacto.Tensor(idx, val, dims, rank=R, factor_dtype=dtype, stream=stream,
+                           line_search=rule)
+        th.set_factors(F0)
+        trace = []
+        for _ in range(n):
+            st_, lo_, al_ = th.gd_iter(want=True)
+            trace.append({"loss": lo_, "alpha": al_})
+        return th, trace
+    n_trace = 5
+    tb, trace_bt = gd_trace(dfacto.BACKTRACKING, n_trace)
+    del tb
+    te, trace_ex = gd_trace(dfacto.EXACT, n_trace)
+    for _ in range(args.warmup):
+        te.gd_iter(want=False)
+    torch.cuda.synchronize()
+    gd_exact_ms = timed(lambda: te.gd_iter(want=False), args.steps)
+    del te
+
     # -- MTTKRP per mode (the dominant kernel) ----------------------------------
     out = torch.empty(max(dims), R, dtype=torch.float32, device=dev)
     mode_ms = []
@@ -666,6 +687,11 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks,
         "gd_iter_per_s": 1e3 / gd_ms, "gd_ms": gd_ms, "gd_alpha": alpha, "gd_loss": loss,
+        "gd_exact": {"iter_per_s": 1e3 / gd_exact_ms, "ms": gd_exact_ms,
+                     "what": "GD with the exact line search (line_search = 1) beside backtracking: "
+                             "objective and step after each of the first %d steps from the same "
+                             "start" % n_trace,
+                     "trace_exact": trace_ex, "trace_backtracking": trace_bt},
         "als_fit": fit, "build_s": build_s, "extras": extras,
     })
 

@@ -1138,10 +1138,21 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
 }
 
-// Shared memory of the double-buffered row passes: W (RT x RT) and two tiles.
+// The tensor-core form of the row passes (RT = 16 or 32) keeps W split into
+// TF32 heads and tails, rows padded to RT + 8 (conflict-free fragment loads).
+template <int RT>
+constexpr bool row_pass_tc() { return RT == 16 || RT == 32; }
+template <int RT>
+constexpr int row_pass_wstride() { return RT + 8; }
+template <int RT>
+constexpr size_t row_pass_w_floats() {
+  return row_pass_tc<RT>() ? 2 * (size_t)RT * row_pass_wstride<RT>() : (size_t)RT * RT;
+}
+
+// Shared memory of the double-buffered row passes: W and two tiles.
 template <int RT>
 constexpr size_t row_pass_smem() {
-  return sizeof(float) * ((size_t)RT * RT + 2 * (size_t)kT * (RT + 4));
+  return sizeof(float) * (row_pass_w_floats<RT>() + 2 * (size_t)kT * (RT + 4));
 }
 
 // Tile t of a row pass in buffer t & 1: for R % 4 == 0 the next tile's copy is
@@ -1215,6 +1226,281 @@ __device__ __forceinline__ void tile_store(const float* __restrict__ tile, int64
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core form of the row passes for RT = 16 and 32.  The products
+// N W (rows x RT times RT x RT) and the Gram of the stored factor (RT x RT
+// over the rows) are dense contractions: they run as mma.sync m16n8k8 with
+// TF32 operands, every FP32 operand split into a TF32 head and a TF32 tail
+// (x = h + l) and each product formed as l h' + h l' + h h' (the dropped l l'
+// term and the tail's rounding are below 2^-21 of the product).  Each k-step
+// of eight starts from a zero accumulator and is added to an FP32 register
+// sum with round-to-nearest adds (the tensor unit's own accumulation is not
+// rounded to nearest, so long accumulator chains inside it drift); the Gram's
+// FP32 sums are folded into FP64 after every tile.  The result has the
+// accuracy of the FP32 FMA form at a fraction of its instructions, which
+// leaves the passes bound by their HBM traffic.  Warp w takes tile rows
+// [32w, 32w + 32) for N W, and output block w of the Gram.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& h, uint32_t& l) {
+  h = to_tf32(x);
+  l = to_tf32(x - __uint_as_float(h));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+// d += a b from split operands: tails first, heads last.
+__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                     uint32_t bh0, uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+  mma_tf32(d, al[0], al[1], al[2], al[3], bh0, bh1);
+  mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+  mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+}
+
+// W (R x R, zero-padded to RT x RT) split into heads Wh and tails Wl, row
+// stride row_pass_wstride<RT>().
+template <int RT>
+__device__ __forceinline__ void stage_w_split(const float* __restrict__ W32, int R, uint32_t* Wh,
+                                              uint32_t* Wl) {
+  constexpr int WS = row_pass_wstride<RT>();
+  for (int e = threadIdx.x; e < RT * WS; e += kT) {
+    const int k = e / WS, c = e % WS;
+    const float w = (k < R && c < R) ? W32[k * R + c] : 0.f;
+    split_tf32(w, Wh[e], Wl[e]);
+  }
+}
+
+// o = rows [m0, m0 + 16) of the tile times W: o[n][0..3] is the mma output
+// fragment of columns [8n, 8n + 8) (rows m0 + gid and m0 + gid + 8, columns
+// 8n + 2 tig and 8n + 2 tig + 1, gid = lane / 4, tig = lane % 4).
+template <int RT>
+__device__ __forceinline__ void tc_rows_times_w(const float* __restrict__ tile, int m0,
+                                                const uint32_t* __restrict__ Wh,
+                                                const uint32_t* __restrict__ Wl,
+                                                float (&o)[RT / 8][4]) {
+  constexpr int LD = RT + 4, WS = row_pass_wstride<RT>(), KS = RT / 8;
+  const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+  uint32_t ah[KS][4], al[KS][4];
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    const float* r0 = tile + (m0 + gid) * LD + 8 * k + tig;
+    const float* r1 = r0 + 8 * LD;
+    split_tf32(r0[0], ah[k][0], al[k][0]);
+    split_tf32(r1[0], ah[k][1], al[k][1]);
+    split_tf32(r0[4], ah[k][2], al[k][2]);
+    split_tf32(r1[4], ah[k][3], al[k][3]);
+  }
+#pragma unroll
+  for (int n = 0; n < RT / 8; ++n) {
+    o[n][0] = o[n][1] = o[n][2] = o[n][3] = 0.f;
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const int e0 = (8 * k + tig) * WS + 8 * n + gid, e1 = e0 + 4 * WS;
+      float t[4] = {0.f, 0.f, 0.f, 0.f};
+      mma3(t, ah[k], al[k], Wh[e0], Wh[e1], Wl[e0], Wl[e1]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) o[n][j] += t[j];
+    }
+  }
+}
+
+// Pass 1, tensor-core form: colsq[vb][c] = sum over the block's rows of
+// (N W)[row, c]^2.  Each lane sums the squares of its fragment entries in
+// FP32; lanes are added by shuffles, warps in FP64 in warp order.
+template <int RT>
+__device__ __forceinline__ void colnorm_rows_tc(const float* __restrict__ N,
+                                                const float* __restrict__ W32, int64_t rows, int R,
+                                                double* __restrict__ colsq, int vb, int vgrid) {
+  constexpr int LD = RT + 4, WS = row_pass_wstride<RT>(), NS = RT / 8;
+  extern __shared__ __align__(16) float row_smem[];
+  uint32_t* Wh = reinterpret_cast<uint32_t*>(row_smem);
+  uint32_t* Wl = Wh + RT * WS;
+  float* tiles = row_smem + row_pass_w_floats<RT>();
+  __shared__ float s_part[kT / 32][RT];
+  stage_w_split<RT>(W32, R, Wh, Wl);
+  for (int e = threadIdx.x; e < 2 * kT * LD; e += kT) tiles[e] = 0.f;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
+  int64_t r0, r1;
+  block_rows(rows, vb, vgrid, r0, r1);
+  float sq[NS][2];
+#pragma unroll
+  for (int n = 0; n < NS; ++n) sq[n][0] = sq[n][1] = 0.f;
+  __syncthreads();
+  row_pass_prefetch<LD>(N, r0, r1, R, tiles);
+  int buf = 0;
+  for (int64_t t0 = r0; t0 < r1; t0 += kT, buf ^= 1) {
+    const int nt = (int)min((int64_t)kT, r1 - t0);
+    __syncthreads();
+    const float* tile = row_pass_tile<LD>(N, t0, r1, R, tiles, buf);
+    __syncthreads();
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int m0 = 32 * warp + 16 * mt;
+      if (m0 >= nt) break;  // warp-uniform
+      float o[NS][4];
+      tc_rows_times_w<RT>(tile, m0, Wh, Wl, o);
+      const bool v0 = m0 + gid < nt, v1 = m0 + gid + 8 < nt;
+#pragma unroll
+      for (int n = 0; n < NS; ++n) {
+        if (v0) { sq[n][0] = fmaf(o[n][0], o[n][0], sq[n][0]); sq[n][1] = fmaf(o[n][1], o[n][1], sq[n][1]); }
+        if (v1) { sq[n][0] = fmaf(o[n][2], o[n][2], sq[n][0]); sq[n][1] = fmaf(o[n][3], o[n][3], sq[n][1]); }
+      }
+    }
+  }
+  // lanes with equal tig hold the same columns: add over gid
+#pragma unroll
+  for (int n = 0; n < NS; ++n)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      float v = sq[n][j];
+      v += __shfl_xor_sync(kFull, v, 4);
+      v += __shfl_xor_sync(kFull, v, 8);
+      v += __shfl_xor_sync(kFull, v, 16);
+      if (gid == 0) s_part[warp][8 * n + 2 * tig + j] = v;
+    }
+  __syncthreads();
+  for (int c = threadIdx.x; c < R; c += kT) {
+    double t = 0.0;
+    for (int w = 0; w < kT / 32; ++w) t += (double)s_part[w][c];
+    colsq[(size_t)vb * R + c] = t;
+  }
+}
+
+// Pass 2, tensor-core form: F[row] = (N W)[row] * inv stored in T, the Gram
+// partials of the stored values gpart[vb][R*R], and with with_ip the fit's
+// inner product ipart[vb] = sum lambda_c F_stored[row, c] N[row, c].  Each
+// warp replaces its 32 tile rows by their stored values and adds their outer
+// products to its own FP32 Gram (every 16 x 8 block of it, as four k-steps of
+// eight rows); the tile is then written to F with coalesced stores.  At the
+// end the warps' Grams are added in FP64, in warp order.
+template <typename T, int RT>
+__device__ __forceinline__ void scale_store_rows_tc(const float* __restrict__ N,
+                                                    const float* __restrict__ W32,
+                                                    const float* __restrict__ inv,
+                                                    const double* __restrict__ lambda, int64_t rows,
+                                                    int R, T* __restrict__ F,
+                                                    double* __restrict__ gpart, bool with_ip,
+                                                    double* __restrict__ ipart, int vb, int vgrid) {
+  constexpr int LD = RT + 4, WS = row_pass_wstride<RT>(), NS = RT / 8, MB = RT / 16;
+  constexpr int NW = kT / 32;
+  extern __shared__ __align__(16) float row_smem[];
+  uint32_t* Wh = reinterpret_cast<uint32_t*>(row_smem);
+  uint32_t* Wl = Wh + RT * WS;
+  float* tiles = row_smem + row_pass_w_floats<RT>();
+  __shared__ float s_sc[RT], s_lm[RT];
+  __shared__ double red[kT];
+  stage_w_split<RT>(W32, R, Wh, Wl);
+  for (int c = threadIdx.x; c < RT; c += kT) {
+    s_sc[c] = c < R ? inv[c] : 0.f;
+    s_lm[c] = (with_ip && c < R) ? (float)lambda[c] : 0.f;
+  }
+  for (int e = threadIdx.x; e < 2 * kT * LD; e += kT) tiles[e] = 0.f;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
+  float g[MB][NS][4];  // this warp's Gram: block (i, j) = rows [16 i, +16) x cols [8 j, +8)
+#pragma unroll
+  for (int i = 0; i < MB; ++i)
+#pragma unroll
+    for (int j = 0; j < NS; ++j) g[i][j][0] = g[i][j][1] = g[i][j][2] = g[i][j][3] = 0.f;
+  double ip = 0.0;
+  int64_t r0, r1;
+  block_rows(rows, vb, vgrid, r0, r1);
+  __syncthreads();
+  row_pass_prefetch<LD>(N, r0, r1, R, tiles);
+  int buf = 0;
+  for (int64_t t0 = r0; t0 < r1; t0 += kT, buf ^= 1) {
+    const int nt = (int)min((int64_t)kT, r1 - t0);
+    __syncthreads();
+    float* tile = row_pass_tile<LD>(N, t0, r1, R, tiles, buf);
+    __syncthreads();
+    float ip32 = 0.f;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int m0 = 32 * warp + 16 * mt;
+      float o[NS][4];
+      tc_rows_times_w<RT>(tile, m0, Wh, Wl, o);
+      __syncwarp();  // every lane has read its operands from these rows
+#pragma unroll
+      for (int n = 0; n < NS; ++n)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int row = m0 + gid + (j >> 1) * 8, col = 8 * n + 2 * tig + (j & 1);
+          float* cell = tile + row * LD + col;
+          const float x = o[n][j] * s_sc[col];
+          const float v = (col < R && row < nt) ? rt_elem(F, x) : 0.f;
+          ip32 = fmaf(s_lm[col] * v, *cell, ip32);
+          *cell = v;
+        }
+    }
+    ip += (double)ip32;
+    __syncwarp();  // the warp's rows hold the stored values
+    // Gram of the warp's 32 stored rows: four k-steps of eight rows
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const float* p0 = tile + (32 * warp + 8 * ks + tig) * LD;
+      const float* p1 = p0 + 4 * LD;
+      uint32_t ah[MB][4], al[MB][4], bh[NS][2], bl[NS][2];
+#pragma unroll
+      for (int i = 0; i < MB; ++i) {
+        split_tf32(p0[16 * i + gid], ah[i][0], al[i][0]);
+        split_tf32(p0[16 * i + gid + 8], ah[i][1], al[i][1]);
+        split_tf32(p1[16 * i + gid], ah[i][2], al[i][2]);
+        split_tf32(p1[16 * i + gid + 8], ah[i][3], al[i][3]);
+      }
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        split_tf32(p0[8 * j + gid], bh[j][0], bl[j][0]);
+        split_tf32(p1[8 * j + gid], bh[j][1], bl[j][1]);
+      }
+#pragma unroll
+      for (int i = 0; i < MB; ++i)
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          float t[4] = {0.f, 0.f, 0.f, 0.f};
+          mma3(t, ah[i], al[i], bh[j][0], bh[j][1], bl[j][0], bl[j][1]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) g[i][j][q] += t[q];
+        }
+    }
+    __syncthreads();
+    tile_store<LD>(tile, t0, nt, R, F);
+  }
+  if (with_ip) {
+    const double t = block_sum(ip, red);
+    if (threadIdx.x == 0) ipart[vb] = t;
+  }
+  // add the warps' Grams in FP64, in warp order (through the tile space:
+  // NW x RT x RT floats <= 2 kT LD floats)
+  __syncthreads();
+  float* gs = tiles;
+#pragma unroll
+  for (int i = 0; i < MB; ++i)
+#pragma unroll
+    for (int j = 0; j < NS; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int a = 16 * i + gid + (q >> 1) * 8, c = 8 * j + 2 * tig + (q & 1);
+        gs[(warp * RT + a) * RT + c] = g[i][j][q];
+      }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RT * RT; e += kT) {
+    const int a = e / RT, c = e % RT;
+    if (a < R && c < R) {
+      double t = 0.0;
+      for (int w = 0; w < NW; ++w) t += (double)gs[w * RT * RT + e];
+      gpart[(size_t)vb * R * R + a * R + c] = t;
+    }
+  }
+}
+
 // Pass 1: colsq[vb][c] = sum over the block's rows of (N W)[row, c]^2.  A tile
 // of kT rows is loaded into shared memory with coalesced loads; thread t then
 // takes row t of the tile.  Each thread sums its rows in FP32; the block adds
@@ -1223,12 +1509,16 @@ template <int RT>
 __device__ __forceinline__ void colnorm_rows_body(const float* __restrict__ N,
                                                   const float* __restrict__ W32, int64_t rows, int R,
                                                   double* __restrict__ colsq, int vb, int vgrid) {
+  if constexpr (row_pass_tc<RT>()) {
+    colnorm_rows_tc<RT>(N, W32, rows, R, colsq, vb, vgrid);
+    return;
+  }
   using PS = PassShape<RT>;
   constexpr int CW = PS::CW, LD = PS::LD;
   static_assert(LD >= RT + 1, "the tile doubles as the FP64 reduction area");
   extern __shared__ __align__(16) float row_smem[];  // row_pass_smem<RT>() bytes
   float* Ws = row_smem;
-  float* tiles = row_smem + RT * RT;
+  float* tiles = row_smem + row_pass_w_floats<RT>();
   stage_w<RT>(W32, R, Ws);
   for (int e = threadIdx.x; e < 2 * kT * LD; e += kT) tiles[e] = 0.f;
   int64_t r0, r1;
@@ -1288,11 +1578,15 @@ __device__ __forceinline__ void scale_store_rows_body(const float* __restrict__ 
                                                       int R, T* __restrict__ F,
                                                       double* __restrict__ gpart, bool with_ip,
                                                       double* __restrict__ ipart, int vb, int vgrid) {
+  if constexpr (row_pass_tc<RT>()) {
+    scale_store_rows_tc<T, RT>(N, W32, inv, lambda, rows, R, F, gpart, with_ip, ipart, vb, vgrid);
+    return;
+  }
   using PS = PassShape<RT>;
   constexpr int CW = PS::CW, LD = PS::LD, NB4 = PS::NB4, NBLK = PS::NBLK, NGRP = PS::NGRP;
   extern __shared__ __align__(16) float row_smem[];  // row_pass_smem<RT>() bytes
   float* Ws = row_smem;
-  float* tiles = row_smem + RT * RT;
+  float* tiles = row_smem + row_pass_w_floats<RT>();
   __shared__ float s_sc[RT], s_lm[RT];
   __shared__ double red[kT];
   stage_w<RT>(W32, R, Ws);
