@@ -140,10 +140,13 @@ __global__ void make_keys_chain(const int32_t* __restrict__ idx, int64_t nnz, in
   }
 }
 
-// Per-tile digit counts, written digit-major: cnt[d * ntiles + tile].
+// Per-tile digit counts, written digit-major: cnt[d * ntiles + tile] (scanned
+// into output offsets afterwards), and tile-major: lcnt[tile * 256 + d] (kept
+// for the tile's own digit order in radix_scatter).
 __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __restrict__ key,
                                                           int64_t n, int shift,
-                                                          int32_t* __restrict__ cnt, int64_t ntiles) {
+                                                          int32_t* __restrict__ cnt,
+                                                          int32_t* __restrict__ lcnt, int64_t ntiles) {
   __shared__ int32_t s_cnt[kDigits];
   s_cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -164,21 +167,52 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __res
   }
   __syncthreads();
   cnt[(int64_t)threadIdx.x * ntiles + blockIdx.x] = s_cnt[threadIdx.x];
+  lcnt[(int64_t)blockIdx.x * kDigits + threadIdx.x] = s_cnt[threadIdx.x];
 }
 
 // Stable scatter of one tile: element order inside a tile is round, then warp,
-// then lane, and equal digits keep that order.
+// then lane, and equal digits keep that order.  The tile's elements are first
+// placed in that order, grouped by digit, in shared memory; then thread t
+// copies out positions t, t + 256, ...: consecutive threads write consecutive
+// positions of one digit's output run, so the writes are coalesced runs
+// instead of one scattered element per digit and round.
+constexpr size_t kScatterSmem = (sizeof(uint64_t) + sizeof(uint32_t)) * kSortTile +
+                                sizeof(int32_t) * (kSortThreads / 32 + 3) * kDigits;
+
 __global__ void __launch_bounds__(kSortThreads) radix_scatter(
     const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, const int32_t* __restrict__ ofs,
-    int64_t ntiles) {
+    const int32_t* __restrict__ lcnt, int64_t ntiles) {
   constexpr int kWarps = kSortThreads / 32;
-  __shared__ int32_t s_cnt[kWarps][kDigits];
-  __shared__ int32_t s_run[kDigits];
+  extern __shared__ __align__(16) unsigned char sort_smem[];  // kScatterSmem bytes
+  uint64_t* s_key = reinterpret_cast<uint64_t*>(sort_smem);              // [kSortTile]
+  uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kSortTile);       // [kSortTile]
+  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_val + kSortTile);         // [kWarps][kDigits]
+  int32_t* s_run = s_cnt + kWarps * kDigits;                              // [kDigits]
+  int32_t* s_lstart = s_run + kDigits;                                    // [kDigits]
+  int32_t* s_gofs = s_lstart + kDigits;                                   // [kDigits]
+  __shared__ int32_t s_wsum[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  s_run[threadIdx.x] = ofs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  const int tn = (int)min((int64_t)kSortTile, n - base);
+  {  // the tile's digit starts: exclusive scan of its counts (one digit per thread)
+    const int d = threadIdx.x;
+    const int c = lcnt[(int64_t)blockIdx.x * kDigits + d];
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    int pre = 0;
+    for (int w = 0; w < warp; ++w) pre += s_wsum[w];
+    s_lstart[d] = pre + x - c;
+    s_run[d] = pre + x - c;
+    s_gofs[d] = ofs[(int64_t)d * ntiles + blockIdx.x];
+  }
   // the next round's element is loaded while this round is ranked
   int64_t i_next = base + threadIdx.x;
   uint64_t k_next = i_next < n ? kin[i_next] : 0;
@@ -197,28 +231,35 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(
     const unsigned peers = __match_any_sync(kFull, d);
     const int rank = __popc(peers & lt);
 #pragma unroll
-    for (int q = 0; q < kDigits / 32; ++q) s_cnt[warp][lane + 32 * q] = 0;
+    for (int q = 0; q < kDigits / 32; ++q) s_cnt[warp * kDigits + lane + 32 * q] = 0;
     __syncwarp();
-    if (ok && rank == 0) s_cnt[warp][d] = __popc(peers);
+    if (ok && rank == 0) s_cnt[warp * kDigits + d] = __popc(peers);
     __syncthreads();
     {
       const int dd = threadIdx.x;  // one digit per thread
       int32_t run = s_run[dd];
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) {
-        const int32_t c = s_cnt[w][dd];
-        s_cnt[w][dd] = run;
+        const int32_t c = s_cnt[w * kDigits + dd];
+        s_cnt[w * kDigits + dd] = run;
         run += c;
       }
       s_run[dd] = run;
     }
     __syncthreads();
     if (ok) {
-      const int64_t pos = (int64_t)s_cnt[warp][d] + rank;
-      kout[pos] = k;
-      vout[pos] = v;
+      const int lp = s_cnt[warp * kDigits + d] + rank;
+      s_key[lp] = k;
+      s_val[lp] = v;
     }
     __syncthreads();
+  }
+  for (int p = threadIdx.x; p < tn; p += kSortThreads) {
+    const uint64_t k = s_key[p];
+    const int d = (int)((k >> shift) & 0xff);
+    const int64_t gp = (int64_t)s_gofs[d] + (p - s_lstart[d]);
+    kout[gp] = k;
+    vout[gp] = s_val[p];
   }
 }
 
@@ -342,18 +383,21 @@ cudaError_t radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, i
   const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
   int32_t* cnt = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&cnt),
-                                  sizeof(int32_t) * kDigits * ntiles, s);
+                                  sizeof(int32_t) * 2 * kDigits * ntiles, s);
   if (e != cudaSuccess) return e;
+  int32_t* lcnt = cnt + kDigits * ntiles;
+  e = ensure_dynamic_smem(reinterpret_cast<const void*>(radix_scatter), kScatterSmem);
   const int passes = (nbits + 7) / 8;
   uint64_t *ki = k0, *ko = k1;
   uint32_t *vi = v0, *vo = v1;
   for (int pass = 0; pass < passes && e == cudaSuccess; ++pass) {
     const int shift = lo_bit + 8 * pass;
-    radix_hist<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n, shift, cnt, ntiles); DF_COUNT();
+    radix_hist<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n, shift, cnt, lcnt, ntiles); DF_COUNT();
     e = cudaGetLastError();
     if (e == cudaSuccess) e = exclusive_scan_i32(cnt, cnt, kDigits * ntiles, s);
     if (e == cudaSuccess) {
-      radix_scatter<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, cnt, ntiles); DF_COUNT();
+      radix_scatter<<<(unsigned)ntiles, kSortThreads, kScatterSmem, s>>>(ki, vi, ko, vo, n, shift, cnt,
+                                                                          lcnt, ntiles); DF_COUNT();
       e = cudaGetLastError();
     }
     std::swap(ki, ko);
