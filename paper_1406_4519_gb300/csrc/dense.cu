@@ -1313,6 +1313,90 @@ __device__ __forceinline__ void tc_rows_times_w(const float* __restrict__ tile, 
   }
 }
 
+// Per-warp Gram on the tensor cores: g += X[rows]^T Y[rows] over the 32 tile
+// rows [row0, row0 + 32) (four k-steps of eight rows; tiles of row stride
+// RT + 4).  g[i][j] is the mma output fragment of the 16 x 8 block at rows
+// [16 i, +16) and columns [8 j, +8).
+template <int RT>
+__device__ __forceinline__ void warp_gram_acc(const float* __restrict__ X, const float* __restrict__ Y,
+                                              int row0, float (&g)[RT / 16][RT / 8][4]) {
+  constexpr int LD = RT + 4, MB = RT / 16, NS = RT / 8;
+  const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    const float* x0 = X + (row0 + 8 * ks + tig) * LD;
+    const float* x1 = x0 + 4 * LD;
+    const float* y0 = Y + (row0 + 8 * ks + tig) * LD;
+    const float* y1 = y0 + 4 * LD;
+    uint32_t ah[MB][4], al[MB][4], bh[NS][2], bl[NS][2];
+#pragma unroll
+    for (int i = 0; i < MB; ++i) {
+      split_tf32(x0[16 * i + gid], ah[i][0], al[i][0]);
+      split_tf32(x0[16 * i + gid + 8], ah[i][1], al[i][1]);
+      split_tf32(x1[16 * i + gid], ah[i][2], al[i][2]);
+      split_tf32(x1[16 * i + gid + 8], ah[i][3], al[i][3]);
+    }
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      split_tf32(y0[8 * j + gid], bh[j][0], bl[j][0]);
+      split_tf32(y1[8 * j + gid], bh[j][1], bl[j][1]);
+    }
+#pragma unroll
+    for (int i = 0; i < MB; ++i)
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        float t[4] = {0.f, 0.f, 0.f, 0.f};
+        mma3(t, ah[i], al[i], bh[j][0], bh[j][1], bl[j][0], bl[j][1]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) g[i][j][q] += t[q];
+      }
+  }
+}
+
+// The warps' Grams added in FP64 in warp order, through `scratch`
+// (kT / 32 * RT * RT floats): warps [0, nw) into gpart[vb][R*R], and with
+// gpart2 warps [nw, 2 nw) into gpart2[vb][R*R].  Called by all threads after
+// the last use of `scratch` as a tile.
+template <int RT>
+__device__ __forceinline__ void fold_warp_grams(const float (&g)[RT / 16][RT / 8][4], float* scratch,
+                                                int R, double* __restrict__ gpart, int vb,
+                                                int nw = kT / 32, double* __restrict__ gpart2 = nullptr) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < RT / 16; ++i)
+#pragma unroll
+    for (int j = 0; j < RT / 8; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int a = 16 * i + gid + (q >> 1) * 8, c = 8 * j + 2 * tig + (q & 1);
+        scratch[(warp * RT + a) * RT + c] = g[i][j][q];
+      }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RT * RT; e += kT) {
+    const int a = e / RT, c = e % RT;
+    if (a < R && c < R) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += (double)scratch[w * RT * RT + e];
+      gpart[(size_t)vb * R * R + a * R + c] = t;
+      if (gpart2) {
+        double t2 = 0.0;
+        for (int w = nw; w < 2 * nw; ++w) t2 += (double)scratch[w * RT * RT + e];
+        gpart2[(size_t)vb * R * R + a * R + c] = t2;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int RT>
+__device__ __forceinline__ void zero_gram(float (&g)[RT / 16][RT / 8][4]) {
+#pragma unroll
+  for (int i = 0; i < RT / 16; ++i)
+#pragma unroll
+    for (int j = 0; j < RT / 8; ++j) g[i][j][0] = g[i][j][1] = g[i][j][2] = g[i][j][3] = 0.f;
+}
+
 // Pass 1, tensor-core form: colsq[vb][c] = sum over the block's rows of
 // (N W)[row, c]^2.  Each lane sums the squares of its fragment entries in
 // FP32; lanes are added by shuffles, warps in FP64 in warp order.
@@ -1391,7 +1475,6 @@ __device__ __forceinline__ void scale_store_rows_tc(const float* __restrict__ N,
                                                     double* __restrict__ gpart, bool with_ip,
                                                     double* __restrict__ ipart, int vb, int vgrid) {
   constexpr int LD = RT + 4, WS = row_pass_wstride<RT>(), NS = RT / 8, MB = RT / 16;
-  constexpr int NW = kT / 32;
   extern __shared__ __align__(16) float row_smem[];
   uint32_t* Wh = reinterpret_cast<uint32_t*>(row_smem);
   uint32_t* Wl = Wh + RT * WS;
@@ -1406,10 +1489,7 @@ __device__ __forceinline__ void scale_store_rows_tc(const float* __restrict__ N,
   for (int e = threadIdx.x; e < 2 * kT * LD; e += kT) tiles[e] = 0.f;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
   float g[MB][NS][4];  // this warp's Gram: block (i, j) = rows [16 i, +16) x cols [8 j, +8)
-#pragma unroll
-  for (int i = 0; i < MB; ++i)
-#pragma unroll
-    for (int j = 0; j < NS; ++j) g[i][j][0] = g[i][j][1] = g[i][j][2] = g[i][j][3] = 0.f;
+  zero_gram<RT>(g);
   double ip = 0.0;
   int64_t r0, r1;
   block_rows(rows, vb, vgrid, r0, r1);
@@ -1442,34 +1522,7 @@ __device__ __forceinline__ void scale_store_rows_tc(const float* __restrict__ N,
     }
     ip += (double)ip32;
     __syncwarp();  // the warp's rows hold the stored values
-    // Gram of the warp's 32 stored rows: four k-steps of eight rows
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      const float* p0 = tile + (32 * warp + 8 * ks + tig) * LD;
-      const float* p1 = p0 + 4 * LD;
-      uint32_t ah[MB][4], al[MB][4], bh[NS][2], bl[NS][2];
-#pragma unroll
-      for (int i = 0; i < MB; ++i) {
-        split_tf32(p0[16 * i + gid], ah[i][0], al[i][0]);
-        split_tf32(p0[16 * i + gid + 8], ah[i][1], al[i][1]);
-        split_tf32(p1[16 * i + gid], ah[i][2], al[i][2]);
-        split_tf32(p1[16 * i + gid + 8], ah[i][3], al[i][3]);
-      }
-#pragma unroll
-      for (int j = 0; j < NS; ++j) {
-        split_tf32(p0[8 * j + gid], bh[j][0], bl[j][0]);
-        split_tf32(p1[8 * j + gid], bh[j][1], bl[j][1]);
-      }
-#pragma unroll
-      for (int i = 0; i < MB; ++i)
-#pragma unroll
-        for (int j = 0; j < NS; ++j) {
-          float t[4] = {0.f, 0.f, 0.f, 0.f};
-          mma3(t, ah[i], al[i], bh[j][0], bh[j][1], bl[j][0], bl[j][1]);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) g[i][j][q] += t[q];
-        }
-    }
+    warp_gram_acc<RT>(tile, tile, 32 * warp, g);
     __syncthreads();
     tile_store<LD>(tile, t0, nt, R, F);
   }
@@ -1477,28 +1530,7 @@ __device__ __forceinline__ void scale_store_rows_tc(const float* __restrict__ N,
     const double t = block_sum(ip, red);
     if (threadIdx.x == 0) ipart[vb] = t;
   }
-  // add the warps' Grams in FP64, in warp order (through the tile space:
-  // NW x RT x RT floats <= 2 kT LD floats)
-  __syncthreads();
-  float* gs = tiles;
-#pragma unroll
-  for (int i = 0; i < MB; ++i)
-#pragma unroll
-    for (int j = 0; j < NS; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int a = 16 * i + gid + (q >> 1) * 8, c = 8 * j + 2 * tig + (q & 1);
-        gs[(warp * RT + a) * RT + c] = g[i][j][q];
-      }
-  __syncthreads();
-  for (int e = threadIdx.x; e < RT * RT; e += kT) {
-    const int a = e / RT, c = e % RT;
-    if (a < R && c < R) {
-      double t = 0.0;
-      for (int w = 0; w < NW; ++w) t += (double)gs[w * RT * RT + e];
-      gpart[(size_t)vb * R * R + a * R + c] = t;
-    }
-  }
+  fold_warp_grams<RT>(g, tiles, R, gpart, vb);  // NW x RT x RT floats <= 2 kT LD floats
 }
 
 // Pass 1: colsq[vb][c] = sum over the block's rows of (N W)[row, c]^2.  A tile
@@ -1745,6 +1777,83 @@ __device__ __forceinline__ void store_gram_partial(const float (&a32)[16], doubl
 // (F row t times Gamma, same arithmetic order as the other row passes) into
 // the N tile, which is then stored with coalesced stores.  Dynamic shared
 // memory: Gamma (RT x RT) and two tiles.
+// Tensor-core form of gd_rows for RT = 16 and 32 (the split TF32 products of
+// the ALS row passes): each warp forms the gradient of its 32 tile rows from
+// F Gamma; then warp w < 4 adds G^T G and warp w + 4 adds F^T G over the rows
+// of warps w and w + 4 (one Gram per warp keeps the registers), and the warps'
+// partials are added in FP64 in warp order.  Dynamic shared memory: Gamma
+// split into heads and tails, and two tiles.
+template <typename T, int RT>
+__device__ __forceinline__ void gd_rows_tc(const float* __restrict__ N, const T* __restrict__ F,
+                                           const float* __restrict__ Gam32, int64_t rows, int R,
+                                           float* __restrict__ grad, double* __restrict__ gpart_gg,
+                                           double* __restrict__ gpart_fg,
+                                           double* __restrict__ spart) {
+  constexpr int LD = RT + 4, WS = row_pass_wstride<RT>(), NS = RT / 8, MB = RT / 16;
+  extern __shared__ __align__(16) float dyn[];
+  uint32_t* Wh = reinterpret_cast<uint32_t*>(dyn);
+  uint32_t* Wl = Wh + RT * WS;
+  float* tN = dyn + row_pass_w_floats<RT>();  // [kT * LD] N, then grad
+  float* tF = tN + kT * LD;                   // [kT * LD] F
+  __shared__ double red[kT];
+  stage_w_split<RT>(Gam32, R, Wh, Wl);
+  for (int e = threadIdx.x; e < 2 * kT * LD; e += kT) tN[e] = 0.f;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gid = lane >> 2, tig = lane & 3;
+  constexpr int HW = kT / 64;  // warps per Gram
+  float g[MB][NS][4];  // G^T G (warps < HW) or F^T G (warps >= HW)
+  zero_gram<RT>(g);
+  const bool is_gg = warp < HW;
+  const int wr = is_gg ? warp : warp - HW;  // rows of warps wr and wr + HW
+  double ad[3] = {0.0, 0.0, 0.0};
+  int64_t r0, r1;
+  block_rows(rows, blockIdx.x, gridDim.x, r0, r1);
+  for (int64_t t0 = r0; t0 < r1; t0 += kT) {
+    const int nt = (int)min((int64_t)kT, r1 - t0);
+    __syncthreads();
+    tile_load<LD>(N, t0, nt, R, tN);
+    tile_load_T<LD>(F, t0, nt, R, tF);
+    __syncthreads();
+    if ((int)threadIdx.x >= nt) {  // rows past the tile's end add nothing
+      for (int c = 0; c < RT; ++c) {
+        tN[threadIdx.x * LD + c] = 0.f;
+        tF[threadIdx.x * LD + c] = 0.f;
+      }
+    }
+    __syncwarp();
+    float af[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int m0 = 32 * warp + 16 * mt;
+      float o[NS][4];
+      tc_rows_times_w<RT>(tF, m0, Wh, Wl, o);
+#pragma unroll
+      for (int n = 0; n < NS; ++n)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int row = m0 + gid + (j >> 1) * 8, col = 8 * n + 2 * tig + (j & 1);
+          float* cell = tN + row * LD + col;
+          const float nv = *cell;
+          const float gv = o[n][j] - nv;  // 0 in padding rows and columns
+          af[0] = fmaf(gv, gv, af[0]);
+          af[1] = fmaf(gv, nv, af[1]);
+          af[2] = fmaf(tF[row * LD + col], nv, af[2]);
+          *cell = gv;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) ad[t] += (double)af[t];
+    __syncthreads();  // every warp's gradient rows are in tN
+    warp_gram_acc<RT>(is_gg ? tN : tF, tN, 32 * wr, g);
+    warp_gram_acc<RT>(is_gg ? tN : tF, tN, 32 * (wr + HW), g);
+    tile_store<LD>(tN, t0, nt, R, grad);
+  }
+  for (int t = 0; t < 3; ++t) {
+    const double v = block_sum(ad[t], red);
+    if (threadIdx.x == 0) spart[(size_t)blockIdx.x * 3 + t] = v;
+  }
+  fold_warp_grams<RT>(g, tN, R, gpart_gg, blockIdx.x, HW, gpart_fg);
+}
+
 template <typename T, int RT>
 __global__ void __launch_bounds__(kT, 2) gd_rows(const float* __restrict__ N, const T* __restrict__ F,
                                                  const float* __restrict__ Gam32, int64_t rows, int R,
@@ -1752,6 +1861,10 @@ __global__ void __launch_bounds__(kT, 2) gd_rows(const float* __restrict__ N, co
                                                  double* __restrict__ gpart_gg,
                                                  double* __restrict__ gpart_fg,
                                                  double* __restrict__ spart) {
+  if constexpr (row_pass_tc<RT>()) {
+    gd_rows_tc<T, RT>(N, F, Gam32, rows, R, grad, gpart_gg, gpart_fg, spart);
+    return;
+  }
   using PS = PassShape<RT>;
   constexpr int CW = PS::CW, LD = PS::LD, NB4 = PS::NB4, NBLK = PS::NBLK, NGRP = PS::NGRP;
   extern __shared__ __align__(16) float dyn[];
@@ -1848,6 +1961,8 @@ __global__ void __launch_bounds__(kT, 2) gd_update_gram(T* __restrict__ F, const
   float a32[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) a32[q] = 0.f;
+  float g[RT / 16 > 0 ? RT / 16 : 1][RT / 8][4];  // tensor-core Gram (RT = 16, 32)
+  if constexpr (row_pass_tc<RT>()) zero_gram<RT>(g);
   int64_t r0, r1;
   block_rows(rows, blockIdx.x, gridDim.x, r0, r1);
   for (int64_t t0 = r0; t0 < r1; t0 += kT) {
@@ -1860,21 +1975,31 @@ __global__ void __launch_bounds__(kT, 2) gd_update_gram(T* __restrict__ F, const
       float* frow = tF + threadIdx.x * LD;
       const float* grow = tG + threadIdx.x * LD;
       for (int c = 0; c < R; ++c) frow[c] = rt_elem(F, frow[c] - step * grow[c]);
+    } else {  // rows past the tile's end add nothing to the Gram
+      float* frow = tF + threadIdx.x * LD;
+      for (int c = 0; c < RT; ++c) frow[c] = 0.f;
     }
     __syncthreads();
     tile_store<LD>(tF, t0, nt, R, F);
-    for (int i = grp; grp < NGRP && i < nt; i += NGRP) {
-      const float4 xv = *reinterpret_cast<const float4*>(tF + i * LD + 4 * bi);
-      const float4 yv = *reinterpret_cast<const float4*>(tF + i * LD + 4 * bj);
-      const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
+    if constexpr (row_pass_tc<RT>()) {
+      warp_gram_acc<RT>(tF, tF, 32 * (threadIdx.x >> 5), g);  // rows >= nt are zero
+    } else {
+      for (int i = grp; grp < NGRP && i < nt; i += NGRP) {
+        const float4 xv = *reinterpret_cast<const float4*>(tF + i * LD + 4 * bi);
+        const float4 yv = *reinterpret_cast<const float4*>(tF + i * LD + 4 * bj);
+        const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int w = 0; w < 4; ++w) a32[u * 4 + w] = fmaf(xa[u], ya[w], a32[u * 4 + w]);
+          for (int w = 0; w < 4; ++w) a32[u * 4 + w] = fmaf(xa[u], ya[w], a32[u * 4 + w]);
+      }
     }
   }
   __syncthreads();
-  store_gram_partial<RT>(a32, reinterpret_cast<double*>(tF), R, gpart, blockIdx.x);
+  if constexpr (row_pass_tc<RT>())
+    fold_warp_grams<RT>(g, tF, R, gpart, blockIdx.x);
+  else
+    store_gram_partial<RT>(a32, reinterpret_cast<double*>(tF), R, gpart, blockIdx.x);
 }
 
 // Opt a kernel in to `Bytes` of dynamic shared memory (above the default
@@ -2226,7 +2351,7 @@ dfacto_status gd_step_rows(dfacto_t* h) {
     if (!h->gram_valid[m] && (st = gram_of_factor(h, m)) != DFACTO_OK) return st;
   DF_CUDA(h, cudaMemsetAsync(h->scal + kG2, 0, sizeof(double), s));
   constexpr int LD = PassShape<RT>::LD;
-  const size_t smem_rows = sizeof(float) * ((size_t)RT * RT + 2 * (size_t)kT * LD);
+  const size_t smem_rows = sizeof(float) * (row_pass_w_floats<RT>() + 2 * (size_t)kT * LD);
   const size_t smem_upd = sizeof(float) * 2 * (size_t)kT * LD;
   allow_smem(gd_rows<T, RT>, smem_rows);
   allow_smem(gd_update_gram<T, RT>, smem_upd);
