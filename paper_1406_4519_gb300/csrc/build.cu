@@ -14,11 +14,12 @@
 // (o, f, in) keys take two stable runs (first by `in`, then by (o, f)) with
 // the nonzero's position as payload.
 //
-// The three modes are sorted as a chain.  Mode m's sorted order ascends in its
-// row axis m, which is the `in` axis of mode m - 1, so a stable sort of that
-// order by (o, f) alone yields mode m - 1's (o, f, in) order.  For 64-bit keys
-// the next mode's key is a bit rotation of the sorted key (every axis is in
-// it), and its sort skips the low `in` bits.
+// The three modes are sorted as a chain m, m + 1, m + 2.  Mode m's sorted
+// order is lexicographic in (m, m + 2, m + 1); mode m + 1 wants
+// (m + 1, m, m + 2), which is that order with axis m + 1 moved to the front,
+// so a stable sort by mode m + 1's row axis o alone yields it (equal o keep
+// their (f, in) order).  For 64-bit keys the next mode's key is a bit rotation
+// of the sorted key (every axis is in it), and its sort reads only the o bits.
 #include <algorithm>
 
 #include "device.cuh"
@@ -96,14 +97,14 @@ __global__ void make_keys64_val(const int32_t* __restrict__ idx, const float* __
 }
 
 // Key of the next mode of the chain from a sorted key of this one (in place):
-// (o, f, in) with widths (bo, bf, bi) becomes (f, in, o), i.e. the next mode's
-// (o, f, in) with widths (bf, bi, bo).
+// (o, f, in) with widths (bo, bf, bi) becomes (in, o, f), i.e. the next mode's
+// (o, f, in) with widths (bi, bo, bf).
 __global__ void rotate_keys(uint64_t* __restrict__ key, int64_t n, int bo, int bf, int bi) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
     const uint64_t k = key[p];
     const uint64_t o = shr64(k, bf + bi), f = low64(shr64(k, bi), bf), in = low64(k, bi);
-    key[p] = shl64(f, bi + bo) | shl64(in, bo) | o;
+    key[p] = shl64(in, bo + bf) | shl64(o, bf) | f;
   }
 }
 
@@ -170,32 +171,63 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __res
   lcnt[(int64_t)blockIdx.x * kDigits + threadIdx.x] = s_cnt[threadIdx.x];
 }
 
-// Stable scatter of one tile: element order inside a tile is round, then warp,
-// then lane, and equal digits keep that order.  The tile's elements are first
-// placed in that order, grouped by digit, in shared memory; then thread t
-// copies out positions t, t + 256, ...: consecutive threads write consecutive
-// positions of one digit's output run, so the writes are coalesced runs
-// instead of one scattered element per digit and round.
+// Stable scatter of one tile.  Warp w holds the tile's elements
+// [512 w, 512 w + 512) (round r, lane l: element 512 w + 32 r + l), so the
+// order (warp, round, lane) is the tile's element order.  Each warp ranks its
+// own elements against its own digit counters (no block barrier per round);
+// one pass over the digits then turns the warps' counts into offsets of the
+// tile's digit-ordered layout in shared memory, and thread t copies out
+// positions t, t + 256, ...: consecutive threads write consecutive positions
+// of one digit's output run, so the writes are coalesced runs.
+constexpr int kSortWarps = kSortThreads / 32;
 constexpr size_t kScatterSmem = (sizeof(uint64_t) + sizeof(uint32_t)) * kSortTile +
-                                sizeof(int32_t) * (kSortThreads / 32 + 3) * kDigits;
+                                sizeof(int32_t) * (kSortWarps + 2) * kDigits;
 
-__global__ void __launch_bounds__(kSortThreads) radix_scatter(
+__global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(
     const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, const int32_t* __restrict__ ofs,
     const int32_t* __restrict__ lcnt, int64_t ntiles) {
-  constexpr int kWarps = kSortThreads / 32;
+  constexpr int kPerWarp = kSortTile / kSortWarps;
   extern __shared__ __align__(16) unsigned char sort_smem[];  // kScatterSmem bytes
   uint64_t* s_key = reinterpret_cast<uint64_t*>(sort_smem);              // [kSortTile]
   uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kSortTile);       // [kSortTile]
-  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_val + kSortTile);         // [kWarps][kDigits]
-  int32_t* s_run = s_cnt + kWarps * kDigits;                              // [kDigits]
-  int32_t* s_lstart = s_run + kDigits;                                    // [kDigits]
+  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_val + kSortTile);         // [kSortWarps][kDigits]
+  int32_t* s_lstart = s_cnt + kSortWarps * kDigits;                       // [kDigits]
   int32_t* s_gofs = s_lstart + kDigits;                                   // [kDigits]
-  __shared__ int32_t s_wsum[kWarps];
+  __shared__ int32_t s_wsum[kSortWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   const int tn = (int)min((int64_t)kSortTile, n - base);
+  const int64_t wbase = base + (int64_t)warp * kPerWarp + lane;
+  // the warp's keys, all loads in flight together (the payloads are read when
+  // they are placed)
+  uint64_t k[kSortRounds];
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = wbase + 32 * r;
+    k[r] = i < n ? kin[i] : 0;
+  }
+  int32_t* wcnt = s_cnt + warp * kDigits;
+#pragma unroll
+  for (int q = 0; q < kDigits / 32; ++q) wcnt[lane + 32 * q] = 0;
+  __syncwarp();
+  // rank of each element among the warp's equal digits before it (< 512: two
+  // ranks per register)
+  uint32_t lr[kSortRounds / 2];
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const bool ok = wbase + 32 * r < n;
+    const int d = ok ? (int)((k[r] >> shift) & 0xff) : kDigits;
+    const unsigned peers = __match_any_sync(kFull, d);
+    const int rank = __popc(peers & lt);
+    const int c = ok ? wcnt[d] : 0;
+    if (r & 1) lr[r / 2] |= (uint32_t)(c + rank) << 16;
+    else lr[r / 2] = (uint32_t)(c + rank);
+    __syncwarp();
+    if (ok && rank == 0) wcnt[d] = c + __popc(peers);
+    __syncwarp();
+  }
   {  // the tile's digit starts: exclusive scan of its counts (one digit per thread)
     const int d = threadIdx.x;
     const int c = lcnt[(int64_t)blockIdx.x * kDigits + d];
@@ -206,59 +238,35 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(
       if (lane >= o) x += y;
     }
     if (lane == 31) s_wsum[warp] = x;
-    __syncthreads();
+    __syncthreads();  // also: every warp's counts are final
     int pre = 0;
     for (int w = 0; w < warp; ++w) pre += s_wsum[w];
-    s_lstart[d] = pre + x - c;
-    s_run[d] = pre + x - c;
+    int run = pre + x - c;
+    s_lstart[d] = run;
     s_gofs[d] = ofs[(int64_t)d * ntiles + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {  // warp w's first position of digit d
+      const int32_t cw = s_cnt[w * kDigits + d];
+      s_cnt[w * kDigits + d] = run;
+      run += cw;
+    }
   }
-  // the next round's element is loaded while this round is ranked
-  int64_t i_next = base + threadIdx.x;
-  uint64_t k_next = i_next < n ? kin[i_next] : 0;
-  uint32_t v_next = i_next < n ? vin[i_next] : 0;
+  __syncthreads();
+#pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t i = i_next;
-    const bool ok = i < n;
-    const uint64_t k = k_next;
-    const uint32_t v = v_next;
-    i_next = i + kSortThreads;
-    if (r + 1 < kSortRounds && i_next < n) {
-      k_next = kin[i_next];
-      v_next = vin[i_next];
+    if (wbase + 32 * r < n) {
+      const int d = (int)((k[r] >> shift) & 0xff);
+      const int lp = wcnt[d] + (int)((lr[r / 2] >> (16 * (r & 1))) & 0xffffu);
+      s_key[lp] = k[r];
+      s_val[lp] = vin[wbase + 32 * r];
     }
-    const int d = ok ? (int)((k >> shift) & 0xff) : kDigits;
-    const unsigned peers = __match_any_sync(kFull, d);
-    const int rank = __popc(peers & lt);
-#pragma unroll
-    for (int q = 0; q < kDigits / 32; ++q) s_cnt[warp * kDigits + lane + 32 * q] = 0;
-    __syncwarp();
-    if (ok && rank == 0) s_cnt[warp * kDigits + d] = __popc(peers);
-    __syncthreads();
-    {
-      const int dd = threadIdx.x;  // one digit per thread
-      int32_t run = s_run[dd];
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) {
-        const int32_t c = s_cnt[w * kDigits + dd];
-        s_cnt[w * kDigits + dd] = run;
-        run += c;
-      }
-      s_run[dd] = run;
-    }
-    __syncthreads();
-    if (ok) {
-      const int lp = s_cnt[warp * kDigits + d] + rank;
-      s_key[lp] = k;
-      s_val[lp] = v;
-    }
-    __syncthreads();
   }
+  __syncthreads();
   for (int p = threadIdx.x; p < tn; p += kSortThreads) {
-    const uint64_t k = s_key[p];
-    const int d = (int)((k >> shift) & 0xff);
+    const uint64_t key = s_key[p];
+    const int d = (int)((key >> shift) & 0xff);
     const int64_t gp = (int64_t)s_gofs[d] + (p - s_lstart[d]);
-    kout[gp] = k;
+    kout[gp] = key;
     vout[gp] = s_val[p];
   }
 }
@@ -505,19 +513,19 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
 
   // Mode order of the sorts (the chain of the header): the start is the mode
   // that minimises the total number of 8-bit digit passes; with 64-bit keys
-  // every start costs the same full sort, and each later mode sorts its o and
-  // f bits only.
+  // every start costs the same full sort, and each later mode sorts its o
+  // bits only.
   int bits[3];
   for (int a = 0; a < 3; ++a) bits[a] = nbits_for(h->dims[a]);
   const bool narrow = bits[0] + bits[1] + bits[2] <= 64;
-  auto of_passes = [&](int m) { return (bits[m] + bits[(m + 2) % 3] + 7) / 8; };
+  auto o_passes = [&](int m) { return (bits[m] + 7) / 8; };
   auto full_passes = [&](int m) {
     const int bo = bits[m], bf = bits[(m + 2) % 3], bi = bits[(m + 1) % 3];
     return narrow ? (bo + bf + bi + 7) / 8 : (bi + 7) / 8 + (bo + bf + 7) / 8;
   };
   int start = 2, best = 1 << 30;
   for (int m = 2; m >= 0; --m) {
-    const int c = full_passes(m) + of_passes((m + 2) % 3) + of_passes((m + 1) % 3);
+    const int c = full_passes(m) + o_passes((m + 1) % 3) + o_passes((m + 2) % 3);
     if (c < best) {
       best = c;
       start = m;
@@ -529,7 +537,7 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
   int prev_bo = 0, prev_bf = 0, prev_bi = 0;
 
   for (int step = 0; step < 3; ++step) {
-    const int mode = (start + 3 - step) % 3;
+    const int mode = (start + step) % 3;
     ModeCSR& M = h->m[mode];
     M.o = mode;
     M.in = (mode + 1) % 3;
@@ -576,19 +584,20 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
       e = cudaGetLastError();
       if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, 0, bo + bf + bi, s, &alt);
     } else if (narrow) {
-      // the previous order ascends in this mode's `in`: sort bits [bi, bi + bf + bo)
+      // the previous order ascends in this mode's (f, in): sort the o bits
       rotate_keys<<<grid_for(n), 256, 0, s>>>(kin, n, prev_bo, prev_bf, prev_bi);
       DF_COUNT();
       e = cudaGetLastError();
-      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, bi, bo + bf + bi, s, &alt);
+      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, bf + bi, bo + bf + bi, s, &alt);
     } else if (chained) {
-      // previous payload = COO positions in an order ascending in this mode's `in`
+      // previous payload = COO positions in an order ascending in this mode's
+      // (f, in): key (o, f), sort the o bits
       make_keys_chain<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, bf, vin, kalt, valt);
       DF_COUNT();
       e = cudaGetLastError();
       std::swap(kin, kalt);
       std::swap(vin, valt);
-      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, 0, bo + bf, s, &alt);
+      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, bf, bo + bf, s, &alt);
     } else {
       make_keys_in<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.in, kin, vin); DF_COUNT();
       e = cudaGetLastError();

@@ -10,13 +10,17 @@ namespace {
 
 constexpr int kFixThreads = 256;
 constexpr int kFixWarps = kFixThreads / 32;
-constexpr int kAhead = 8;  // carry entries a warp loads before adding them
+constexpr int kAheadCols = 32;  // carry values per lane a warp loads before adding them
 
 // One block per CTA c (grid-stride): if c's last partial run belongs to a row r
 // that starts inside c, add up r's partials from CTAs c .. c_last in CTA order
 // (eight warps take interleaved entries, then their sums are added in warp
 // order) and store N[r, :].  Then all blocks zero the rows without fibers.
 // `bad` (nullable) is set when a carry entry does not name the row it should.
+// CPL = columns per lane (R <= 32 * CPL); a warp keeps 32 / CPL entries in
+// flight, which bounds the time of the longest row (a heavy row of a
+// power-law mode spans over a thousand CTAs).
+template <int CPL>
 __global__ void __launch_bounds__(kFixThreads) mttkrp_fixup(
     const int32_t* __restrict__ carry_row, const float* __restrict__ carry,
     const int64_t* __restrict__ fiber_ptr, const int64_t* __restrict__ nz_ptr, float* __restrict__ out,
@@ -32,45 +36,44 @@ __global__ void __launch_bounds__(kFixThreads) mttkrp_fixup(
     const int64_t re = nz_ptr[fiber_ptr[r + 1]];
     const int64_t clast = (re - 1) / P;
     const int64_t ne = clast - c + 1;
-    float s[kMaxColsPerLane];
+    float s[CPL];
 #pragma unroll
-    for (int q = 0; q < kMaxColsPerLane; ++q) s[q] = 0.f;
+    for (int q = 0; q < CPL; ++q) s[q] = 0.f;
     // Warp w adds entries w, w + 8, w + 16, ... in that order; kAhead of them
-    // are loaded before the adds so that their loads overlap (a row of a few
-    // million nonzeros spans over a thousand CTAs).
+    // are loaded before the adds so that their loads overlap.
+    constexpr int kAhead = kAheadCols / CPL;
     for (int64_t j0 = warp; j0 < ne; j0 += (int64_t)kAhead * kFixWarps) {
-      float t[kAhead][kMaxColsPerLane];
+      float t[kAhead][CPL];
 #pragma unroll
       for (int u = 0; u < kAhead; ++u) {
         const int64_t j = j0 + (int64_t)u * kFixWarps;
         const int64_t entry = (j == 0) ? (2 * c + k) : (2 * (c + j));
 #pragma unroll
-        for (int q = 0; q < kMaxColsPerLane; ++q) {
+        for (int q = 0; q < CPL; ++q) {
           const int col = lane + 32 * q;
           t[u][q] = (j < ne && col < R) ? carry[entry * R + col] : 0.f;
         }
       }
+      // Entries past the end hold +0 and are added too (no branch between the
+      // loads and the adds); only the sign of a zero sum can differ.
 #pragma unroll
-      for (int u = 0; u < kAhead; ++u) {
-        if (j0 + (int64_t)u * kFixWarps < ne) {
+      for (int u = 0; u < kAhead; ++u)
 #pragma unroll
-          for (int q = 0; q < kMaxColsPerLane; ++q) s[q] += t[u][q];
-        }
-      }
+        for (int q = 0; q < CPL; ++q) s[q] += t[u][q];
       if (lane < kAhead) {
         const int64_t j = j0 + (int64_t)lane * kFixWarps;
         if (bad && j > 0 && j < ne && carry_row[2 * (c + j)] != r) atomicOr(bad, 1);
       }
     }
 #pragma unroll
-    for (int q = 0; q < kMaxColsPerLane; ++q) {
+    for (int q = 0; q < CPL; ++q) {
       const int col = lane + 32 * q;
       if (col < R) part[warp][col] = s[q];
     }
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
-      for (int q = 0; q < kMaxColsPerLane; ++q) {
+      for (int q = 0; q < CPL; ++q) {
         const int col = lane + 32 * q;
         if (col < R) {
           float t = 0.f;
@@ -104,8 +107,15 @@ cudaError_t launch_mttkrp_fixup(const int32_t* carry_row, const float* carry,
                                 cudaStream_t s) {
   const int64_t zero_blocks = (dim_o + kFixThreads - 1) / kFixThreads;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(std::max(ncta, zero_blocks), 152 * 16));
-  mttkrp_fixup<<<(unsigned)blocks, kFixThreads, 0, s>>>(carry_row, carry, fiber_ptr, nz_ptr, out, R,
-                                                         P, ncta, dim_o, bad);
+  if (R <= 32)
+    mttkrp_fixup<1><<<(unsigned)blocks, kFixThreads, 0, s>>>(carry_row, carry, fiber_ptr, nz_ptr, out,
+                                                              R, P, ncta, dim_o, bad);
+  else if (R <= 64)
+    mttkrp_fixup<2><<<(unsigned)blocks, kFixThreads, 0, s>>>(carry_row, carry, fiber_ptr, nz_ptr, out,
+                                                              R, P, ncta, dim_o, bad);
+  else
+    mttkrp_fixup<kMaxColsPerLane><<<(unsigned)blocks, kFixThreads, 0, s>>>(
+        carry_row, carry, fiber_ptr, nz_ptr, out, R, P, ncta, dim_o, bad);
   DF_COUNT();
   return cudaGetLastError();
 }
@@ -184,13 +194,8 @@ dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out) {
               : launch_walk<float>(cfg.vec, cfg.G, a, ncta, smem, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "mttkrp_walk launch");
   }
-  const int64_t zero_blocks = (M.dim_o + kFixThreads - 1) / kFixThreads;
-  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(std::max(ncta, zero_blocks), 152 * 16));
-  mttkrp_fixup<<<(unsigned)blocks, kFixThreads, 0, h->stream>>>(
-      h->carry_row, h->carry, M.fiber_ptr, M.nz_ptr, out, h->R, P, ncta, M.dim_o,
-      h->flags + kFlagInternal);
-  DF_COUNT();
-  DF_CUDA(h, cudaGetLastError());
+  DF_CUDA(h, launch_mttkrp_fixup(h->carry_row, h->carry, M.fiber_ptr, M.nz_ptr, out, h->R, P, ncta,
+                                 M.dim_o, h->flags + kFlagInternal, h->stream));
   return DFACTO_OK;
 }
 

@@ -80,8 +80,12 @@ def test_csr_appendix_d_bit_exact():
 @pytest.mark.parametrize("dims,nnz,seed", [([200, 150, 100], 10000, 1),
                                            ([37, 1, 53], 1200, 2),
                                            ([1, 1, 1], 1, 3),
-                                           ([5000, 3, 7], 20000, 4)])
+                                           ([5000, 3, 7], 20000, 4),
+                                           ([3, 5000, 7], 20000, 8),
+                                           ([7, 3, 5000], 20000, 9)])
 def test_csr_uniform_bit_exact(dims, nnz, seed):
+    """The chain of sorts starts at the mode whose later modes need the
+    fewest digit passes: the three 5000-long cases start it at each mode."""
     idx, val = synth.uniform_tensor(dims, nnz, seed=seed, device="cuda")
     t = dfacto.Tensor(idx, val, dims, rank=4)
     check_csr(t, idx, val, dims)
