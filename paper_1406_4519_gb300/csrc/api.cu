@@ -168,6 +168,12 @@ dfacto_status convert_factor_in(dfacto_t* h, int m, const void* src, int src_dty
   const int64_t n = (int64_t)h->dims[m] * h->R;
   const void* dsrc = src;
   void* tmp = nullptr;
+  if (!is_device_ptr(src) && src_dtype == h->dtype) {  // same type: one copy into the factor
+    DF_CUDA(h, cudaMemcpyAsync(h->F[m], src, n * elem_size(src_dtype), cudaMemcpyHostToDevice, h->stream));
+    DF_CUDA(h, cudaStreamSynchronize(h->stream));  // caller may free its host buffer
+    h->gram_valid[m] = false;
+    return DFACTO_OK;
+  }
   if (!is_device_ptr(src)) {
     DF_CUDA(h, cudaMallocAsync(&tmp, std::max<size_t>(16, n * elem_size(src_dtype)), h->stream));
     DF_CUDA(h, cudaMemcpyAsync(tmp, src, n * elem_size(src_dtype), cudaMemcpyHostToDevice, h->stream));
@@ -186,6 +192,11 @@ dfacto_status convert_factor_out(dfacto_t* h, int m, void* dst, int dst_dtype) {
   if (is_device_ptr(dst)) {
     cudaError_t e = convert(h->F[m], h->dtype, dst, dst_dtype, n, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "factor conversion");
+    return DFACTO_OK;
+  }
+  if (dst_dtype == h->dtype) {  // same type: one copy out of the factor
+    DF_CUDA(h, cudaMemcpyAsync(dst, h->F[m], n * elem_size(dst_dtype), cudaMemcpyDeviceToHost, h->stream));
+    DF_CUDA(h, cudaStreamSynchronize(h->stream));
     return DFACTO_OK;
   }
   void* tmp = nullptr;
