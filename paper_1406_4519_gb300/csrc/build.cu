@@ -271,7 +271,10 @@ __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(
   }
 }
 
-// After the sort: fiber-start flags, duplicate detection, nz_idx and nz_val.
+// After the sort: fiber-start flags, duplicate detection, nz_idx and nz_val,
+// and the fiber-end bitmask (bit p of end_bits set iff nonzero p is the last
+// of its fiber: p is the last nonzero or p + 1 starts a new fiber; one ballot
+// per warp of 32 consecutive positions).
 // narrow: key = (o,f,in) packed with `in` in the low bi bits.
 // wide:   key = (o,f) packed; `in` comes from the COO through perm.
 // With val_payload the payload holds the value's bits (narrow keys), else the
@@ -281,40 +284,54 @@ __global__ void segment_flags(const uint64_t* __restrict__ key, const uint32_t* 
                               const int32_t* __restrict__ idx, int ai,
                               const float* __restrict__ val, int32_t* __restrict__ head,
                               int32_t* __restrict__ nz_idx, float* __restrict__ nz_val,
-                              int32_t* __restrict__ dup_flag) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+                              uint32_t* __restrict__ end_bits, int32_t* __restrict__ dup_flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // a multiple of 32
+  const int lane = threadIdx.x & 31;
   bool dup = false;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-    const uint64_t k = key[p];
-    const uint32_t pl = perm[p];
-    int32_t in;
-    uint64_t fkey;
-    if (wide) {
-      in = idx[ai * n + pl];
-      fkey = k;
-    } else {
-      in = (int32_t)low64(k, bi);
-      fkey = shr64(k, bi);
-    }
-    int32_t h = 1;
-    if (p > 0) {
-      const uint64_t kp = key[p - 1];
+  // warp-uniform loop: the warp's lanes take 32 consecutive positions from p0
+  for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); p0 < n; p0 += stride) {
+    const int64_t p = p0 + lane;
+    bool endb = false;
+    if (p < n) {
+      const uint64_t k = key[p];
+      const uint32_t pl = perm[p];
+      int32_t in;
+      uint64_t fkey;
       if (wide) {
-        if (kp == k) {
-          h = 0;
-          dup |= (idx[ai * n + perm[p - 1]] == in);
-        }
+        in = idx[ai * n + pl];
+        fkey = k;
       } else {
-        const uint64_t fp = (bi >= 64) ? 0 : (kp >> bi);
-        h = (fp != fkey);
-        dup |= (kp == k);
+        in = (int32_t)low64(k, bi);
+        fkey = shr64(k, bi);
       }
+      int32_t h = 1;
+      if (p > 0) {
+        const uint64_t kp = key[p - 1];
+        if (wide) {
+          if (kp == k) {
+            h = 0;
+            dup |= (idx[ai * n + perm[p - 1]] == in);
+          }
+        } else {
+          const uint64_t fp = (bi >= 64) ? 0 : (kp >> bi);
+          h = (fp != fkey);
+          dup |= (kp == k);
+        }
+      }
+      if (p + 1 >= n) {
+        endb = true;
+      } else {
+        const uint64_t kn = key[p + 1];
+        endb = wide ? (kn != k) : (shr64(kn, bi) != fkey);
+      }
+      head[p] = h;
+      nz_idx[p] = in;
+      nz_val[p] = val_payload ? __uint_as_float(pl) : val[pl];
     }
-    head[p] = h;
-    nz_idx[p] = in;
-    nz_val[p] = val_payload ? __uint_as_float(pl) : val[pl];
+    const unsigned bits = __ballot_sync(kFull, endb);
+    if (lane == 0) end_bits[p0 >> 5] = bits;
   }
-  if (__any_sync(kFull, dup) && (threadIdx.x & 31) == 0) atomicOr(dup_flag, 1);
+  if (__any_sync(kFull, dup) && lane == 0) atomicOr(dup_flag, 1);
 }
 
 __global__ void scatter_fibers(const uint64_t* __restrict__ key, const uint32_t* __restrict__ perm,
@@ -628,8 +645,14 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
     prev_bo = bo;
     prev_bf = bf;
     prev_bi = bi;
+    st = dalloc(h, reinterpret_cast<void**>(&M.end_bits), sizeof(uint32_t) * (size_t)((n + 31) / 32));
+    if (st != DFACTO_OK) {
+      cleanup();
+      return st;
+    }
     segment_flags<<<grid_for(n), 256, 0, s>>>(key, perm, n, bi, wide, narrow, d_idx, M.in, d_val,
-                                             head, M.nz_idx, M.nz_val, h->flags + kFlagDup); DF_COUNT();
+                                             head, M.nz_idx, M.nz_val, M.end_bits,
+                                             h->flags + kFlagDup); DF_COUNT();
     e = cudaGetLastError();
     if (e == cudaSuccess) e = exclusive_scan_i32(head, fid, n, s);
     int32_t last[2] = {0, 0};
@@ -653,18 +676,6 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
     scatter_fibers<<<grid_for(n), 256, 0, s>>>(key, perm, n, bf, bi, wide, head, fid, M.nz_ptr,
                                               M.fiber_idx, M.fiber_row, M.nfib); DF_COUNT();
     row_pointers<<<grid_for(M.dim_o + 1), 256, 0, s>>>(M.fiber_row, M.nfib, M.dim_o, M.fiber_ptr); DF_COUNT();
-    {
-      const size_t words = (size_t)((n + 31) / 32);
-      st = dalloc(h, reinterpret_cast<void**>(&M.end_bits), sizeof(uint32_t) * words);
-      if (st != DFACTO_OK) {
-        cleanup();
-        return st;
-      }
-      e = cudaMemsetAsync(M.end_bits, 0, sizeof(uint32_t) * words, s);
-      if (e == cudaSuccess) {
-        fiber_end_bits<<<grid_for(M.nfib), 256, 0, s>>>(M.nz_ptr, M.nfib, M.end_bits); DF_COUNT();
-      }
-    }
     e = cudaGetLastError();
     if (e != cudaSuccess) {
       cleanup();

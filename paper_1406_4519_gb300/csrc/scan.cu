@@ -42,10 +42,20 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan(const int32_t* in, int
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   if (threadIdx.x == 0) s_run = offsets ? offsets[blockIdx.x] : 0;
-  __syncthreads();
+  // all of the thread's values first (one load latency per tile, not one per
+  // round); each value is read and written by this thread only, so in == out
+  // is fine
+  int32_t xs[kScanRounds];
+#pragma unroll
   for (int r = 0; r < kScanRounds; ++r) {
     const int64_t i = base + (int64_t)r * kScanThreads + threadIdx.x;
-    const int32_t x = (i < n) ? in[i] : 0;
+    xs[r] = (i < n) ? in[i] : 0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kScanRounds; ++r) {
+    const int64_t i = base + (int64_t)r * kScanThreads + threadIdx.x;
+    const int32_t x = xs[r];
     int32_t incl = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
