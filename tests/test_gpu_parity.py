@@ -558,6 +558,34 @@ def test_out_of_range_and_duplicate_coordinates():
     assert e.value.status == dfacto.EDUP
 
 
+def test_build_out_of_device_memory_is_enomem_and_the_device_stays_usable():
+    """A tensor whose dense arrays need ~1 TiB (a 2^31 - 1 long mode at
+    R = 128): the build's allocation is refused, dfacto_build returns ENOMEM
+    after releasing what it had allocated, and the device keeps working: a
+    small tensor built afterwards sweeps like the oracle, and the same huge
+    request is refused the same way a second time."""
+    huge = [2 ** 31 - 1, 2, 2]
+    idx = torch.zeros(3, 1, dtype=torch.int32, device="cuda")
+    val = torch.ones(1, device="cuda")
+    for _ in range(2):
+        with pytest.raises(dfacto.DfactoError) as e:
+            dfacto.Tensor(idx, val, huge, rank=128)
+        assert e.value.status == dfacto.ENOMEM
+        torch.cuda.synchronize()  # no error left on the context
+        dims = [40, 30, 20]
+        sidx, sval = synth.uniform_tensor(dims, 2000, seed=12, device="cuda")
+        F = synth.normal_factors(dims, 4, seed=13, device="cuda")
+        t = dfacto.Tensor(sidx, sval, dims, rank=4)
+        t.set_factors(F)
+        st, fit = t.als_iter()
+        assert st in (dfacto.OK, dfacto.ESINGULAR)
+        ot = as_oracle(sidx, sval, dims)
+        st_o, Fo, lam_o, fit_o = oracle.als_sweep(ot, [f.double().cpu().numpy() for f in F])
+        got = [f.double().cpu().numpy() for f in t.factors()]
+        for m in range(3):
+            assert np.linalg.norm(got[m] - Fo[m]) <= 1e-4 * np.linalg.norm(Fo[m]), m
+
+
 def test_host_inputs_give_the_same_csr():
     dims = [60, 50, 40]
     idx, val = synth.uniform_tensor(dims, 5000, seed=11, device="cpu")

@@ -281,3 +281,38 @@ def test_job_in_the_mix_equals_job_alone(dtype_name, tol, fit_tol):
             got = job.result["factors"][m].double().numpy()
             assert np.linalg.norm(got - alone[m]) <= tol * np.linalg.norm(alone[m]), (i, m)
         assert abs(job.fits[-1] - fit) <= fit_tol, (i, job.fits[-1], fit)
+
+
+@pytest.mark.gpu
+def test_a_request_too_large_for_the_device_fails_alone():
+    """A request whose tensor cannot be allocated on the device (a 2^31 - 1
+    long mode at R = 128, ~1 TiB of dense arrays) is larger than the budget,
+    so it is admitted alone; its build fails with ENOMEM and the request is
+    rejected with that error, while the requests around it are served their
+    three sweeps with results."""
+    import torch
+
+    from paper_1406_4519_gb300 import dfacto, synth
+
+    shapes = [([300, 200, 100], 20000, 8), ([2 ** 31 - 1, 2, 2], 1, 128), ([200, 150, 100], 10000, 16)]
+
+    def maker(i):
+        dims, nnz, R = shapes[i]
+
+        def make():
+            if i == 1:  # one nonzero; the build fails before factors are needed
+                return (torch.zeros(3, 1, dtype=torch.int32, device="cuda"),
+                        torch.ones(1, device="cuda"), None)
+            idx, val = synth.uniform_tensor(dims, nnz, seed=400 + i, device="cuda")
+            return idx, val, synth.normal_factors(dims, R, seed=500 + i, device="cuda")
+        return make
+
+    jobs = [serve.JobSpec(i, 0.001 * i, shapes[i][0], shapes[i][1], shapes[i][2], make=maker(i))
+            for i in range(len(shapes))]
+    done = serve.serve(jobs, max_iters=3, tol=0.0, factor_dtype=dfacto.F32, budget_bytes=1e9)
+    by_id = {j.spec.job_id: j for j in done}
+    assert sorted(by_id) == [0, 1, 2]
+    bad = by_id[1]
+    assert bad.error is not None and "out of memory" in bad.error and bad.result is None
+    for i in (0, 2):
+        assert by_id[i].error is None and by_id[i].iters == 3 and by_id[i].result is not None
