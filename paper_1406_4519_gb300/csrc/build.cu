@@ -7,9 +7,10 @@
 // (X^{n+1})^T, i.e. the fibers; their starts give nz_ptr, their f gives
 // col(M^r) and their o gives row(M^r) (fiber_ptr, empty rows kept).
 //
-// The sort is a least-significant-digit radix sort with 8-bit digits written
-// for this library: per-tile digit histograms, a device-wide scan, and a stable
-// scatter that ranks equal digits inside a warp with __match_any_sync.  Keys
+// The sort is a least-significant-digit radix sort with 8- or 9-bit digits
+// written for this library: per-tile digit histograms, a device-wide scan, and
+// a stable scatter that ranks equal digits inside a warp with
+// __match_any_sync.  Keys
 // of up to 64 bits sort in one run with the nonzero's value as payload; wider
 // (o, f, in) keys take two stable runs (first by `in`, then by (o, f)) with
 // the nonzero's position as payload.
@@ -32,7 +33,7 @@ namespace {
 constexpr int kSortThreads = 256;
 constexpr int kSortRounds = 16;
 constexpr int64_t kSortTile = (int64_t)kSortThreads * kSortRounds;
-constexpr int kDigits = 256;
+constexpr int kMaxDigitBits = 9;  // digits of 8 or 9 bits (256 or 512 bins)
 
 int nbits_for(int64_t dim) {  // bits needed for values 0 .. dim-1
   int b = 0;
@@ -142,14 +143,18 @@ __global__ void make_keys_chain(const int32_t* __restrict__ idx, int64_t nnz, in
 }
 
 // Per-tile digit counts, written digit-major: cnt[d * ntiles + tile] (scanned
-// into output offsets afterwards), and tile-major: lcnt[tile * 256 + d] (kept
-// for the tile's own digit order in radix_scatter).
+// into output offsets afterwards), and tile-major: lcnt[tile * D + d] (kept
+// for the tile's own digit order in radix_scatter).  A digit is BITS bits of
+// the key from `shift`, masked by dmask (the last digit of a range may be
+// narrower).
+template <int BITS>
 __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __restrict__ key,
-                                                          int64_t n, int shift,
+                                                          int64_t n, int shift, uint32_t dmask,
                                                           int32_t* __restrict__ cnt,
                                                           int32_t* __restrict__ lcnt, int64_t ntiles) {
-  __shared__ int32_t s_cnt[kDigits];
-  s_cnt[threadIdx.x] = 0;
+  constexpr int D = 1 << BITS;
+  __shared__ int32_t s_cnt[D];
+  for (int d = threadIdx.x; d < D; d += kSortThreads) s_cnt[d] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   const int lane = threadIdx.x & 31;
@@ -158,17 +163,19 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __res
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-    dg[r] = i < n ? (int)((key[i] >> shift) & 0xff) : kDigits;
+    dg[r] = i < n ? (int)((key[i] >> shift) & dmask) : D;
   }
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const int d = dg[r];
     const unsigned peers = __match_any_sync(kFull, d);
-    if (d < kDigits && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[d], __popc(peers));
+    if (d < D && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[d], __popc(peers));
   }
   __syncthreads();
-  cnt[(int64_t)threadIdx.x * ntiles + blockIdx.x] = s_cnt[threadIdx.x];
-  lcnt[(int64_t)blockIdx.x * kDigits + threadIdx.x] = s_cnt[threadIdx.x];
+  for (int d = threadIdx.x; d < D; d += kSortThreads) {
+    cnt[(int64_t)d * ntiles + blockIdx.x] = s_cnt[d];
+    lcnt[(int64_t)blockIdx.x * D + d] = s_cnt[d];
+  }
 }
 
 // Stable scatter of one tile.  Warp w holds the tile's elements
@@ -180,20 +187,26 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __res
 // positions t, t + 256, ...: consecutive threads write consecutive positions
 // of one digit's output run, so the writes are coalesced runs.
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr size_t kScatterSmem = (sizeof(uint64_t) + sizeof(uint32_t)) * kSortTile +
-                                sizeof(int32_t) * (kSortWarps + 2) * kDigits;
+template <int BITS>
+constexpr size_t scatter_smem() {
+  return (sizeof(uint64_t) + sizeof(uint32_t)) * kSortTile +
+         sizeof(int32_t) * (kSortWarps + 2) * ((size_t)1 << BITS);
+}
 
+template <int BITS>
 __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(
     const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, int64_t n, int shift, const int32_t* __restrict__ ofs,
-    const int32_t* __restrict__ lcnt, int64_t ntiles) {
+    uint32_t* __restrict__ vout, int64_t n, int shift, uint32_t dmask,
+    const int32_t* __restrict__ ofs, const int32_t* __restrict__ lcnt, int64_t ntiles) {
+  constexpr int D = 1 << BITS;
+  constexpr int DPT = D / kSortThreads;  // digits per thread in the digit passes
   constexpr int kPerWarp = kSortTile / kSortWarps;
-  extern __shared__ __align__(16) unsigned char sort_smem[];  // kScatterSmem bytes
+  extern __shared__ __align__(16) unsigned char sort_smem[];  // scatter_smem<BITS>() bytes
   uint64_t* s_key = reinterpret_cast<uint64_t*>(sort_smem);              // [kSortTile]
   uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kSortTile);       // [kSortTile]
-  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_val + kSortTile);         // [kSortWarps][kDigits]
-  int32_t* s_lstart = s_cnt + kSortWarps * kDigits;                       // [kDigits]
-  int32_t* s_gofs = s_lstart + kDigits;                                   // [kDigits]
+  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_val + kSortTile);         // [kSortWarps][D]
+  int32_t* s_lstart = s_cnt + kSortWarps * D;                             // [D]
+  int32_t* s_gofs = s_lstart + D;                                         // [D]
   __shared__ int32_t s_wsum[kSortWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -208,9 +221,9 @@ __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(
     const int64_t i = wbase + 32 * r;
     k[r] = i < n ? kin[i] : 0;
   }
-  int32_t* wcnt = s_cnt + warp * kDigits;
+  int32_t* wcnt = s_cnt + warp * D;
 #pragma unroll
-  for (int q = 0; q < kDigits / 32; ++q) wcnt[lane + 32 * q] = 0;
+  for (int q = 0; q < D / 32; ++q) wcnt[lane + 32 * q] = 0;
   __syncwarp();
   // rank of each element among the warp's equal digits before it (< 512: two
   // ranks per register)
@@ -218,7 +231,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const bool ok = wbase + 32 * r < n;
-    const int d = ok ? (int)((k[r] >> shift) & 0xff) : kDigits;
+    const int d = ok ? (int)((k[r] >> shift) & dmask) : D;
     const unsigned peers = __match_any_sync(kFull, d);
     const int rank = __popc(peers & lt);
     const int c = ok ? wcnt[d] : 0;
@@ -228,10 +241,17 @@ __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(
     if (ok && rank == 0) wcnt[d] = c + __popc(peers);
     __syncwarp();
   }
-  {  // the tile's digit starts: exclusive scan of its counts (one digit per thread)
-    const int d = threadIdx.x;
-    const int c = lcnt[(int64_t)blockIdx.x * kDigits + d];
-    int x = c;
+  {  // the tile's digit starts: exclusive scan of its counts, thread t owns
+     // digits [DPT t, DPT t + DPT)
+    const int d0 = DPT * threadIdx.x;
+    int c[DPT];
+    int sum = 0;
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      c[j] = lcnt[(int64_t)blockIdx.x * D + d0 + j];
+      sum += c[j];
+    }
+    int x = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(kFull, x, o);
@@ -239,23 +259,26 @@ __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(
     }
     if (lane == 31) s_wsum[warp] = x;
     __syncthreads();  // also: every warp's counts are final
-    int pre = 0;
-    for (int w = 0; w < warp; ++w) pre += s_wsum[w];
-    int run = pre + x - c;
-    s_lstart[d] = run;
-    s_gofs[d] = ofs[(int64_t)d * ntiles + blockIdx.x];
+    int run = x - sum;
+    for (int w = 0; w < warp; ++w) run += s_wsum[w];
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {  // warp w's first position of digit d
-      const int32_t cw = s_cnt[w * kDigits + d];
-      s_cnt[w * kDigits + d] = run;
-      run += cw;
+    for (int j = 0; j < DPT; ++j) {
+      const int d = d0 + j;
+      s_lstart[d] = run;
+      s_gofs[d] = ofs[(int64_t)d * ntiles + blockIdx.x];
+#pragma unroll
+      for (int w = 0; w < kSortWarps; ++w) {  // warp w's first position of digit d
+        const int32_t cw = s_cnt[w * D + d];
+        s_cnt[w * D + d] = run;
+        run += cw;
+      }
     }
   }
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     if (wbase + 32 * r < n) {
-      const int d = (int)((k[r] >> shift) & 0xff);
+      const int d = (int)((k[r] >> shift) & dmask);
       const int lp = wcnt[d] + (int)((lr[r / 2] >> (16 * (r & 1))) & 0xffffu);
       s_key[lp] = k[r];
       s_val[lp] = vin[wbase + 32 * r];
@@ -264,7 +287,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(
   __syncthreads();
   for (int p = threadIdx.x; p < tn; p += kSortThreads) {
     const uint64_t key = s_key[p];
-    const int d = (int)((key >> shift) & 0xff);
+    const int d = (int)((key >> shift) & dmask);
     const int64_t gp = (int64_t)s_gofs[d] + (p - s_lstart[d]);
     kout[gp] = key;
     vout[gp] = s_val[p];
@@ -397,39 +420,91 @@ unsigned grid_for(int64_t n, int threads = 256, int64_t cap = 152 * 32) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, cap));
 }
 
+// One radix pass of BITS-bit digits from `shift` (digits masked to the sort's
+// top bit): counts, scan, scatter.
+template <int BITS>
+cudaError_t radix_pass(const uint64_t* ki, const uint32_t* vi, uint64_t* ko, uint32_t* vo, int64_t n,
+                       int shift, int hi_bit, int32_t* cnt, int64_t ntiles, cudaStream_t s) {
+  constexpr int D = 1 << BITS;
+  const int w = std::min(BITS, hi_bit - shift);
+  const uint32_t dmask = (w >= 32) ? 0xffffffffu : ((1u << w) - 1u);
+  int32_t* lcnt = cnt + (int64_t)D * ntiles;
+  cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(radix_scatter<BITS>),
+                                      scatter_smem<BITS>());
+  if (e != cudaSuccess) return e;
+  radix_hist<BITS><<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n, shift, dmask, cnt, lcnt, ntiles);
+  DF_COUNT();
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = exclusive_scan_i32(cnt, cnt, (int64_t)D * ntiles, s);
+  if (e == cudaSuccess) {
+    radix_scatter<BITS><<<(unsigned)ntiles, kSortThreads, scatter_smem<BITS>(), s>>>(
+        ki, vi, ko, vo, n, shift, dmask, cnt, lcnt, ntiles);
+    DF_COUNT();
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+// Digit passes for an nbits-wide range: the fewest passes of at most
+// kMaxDigitBits bits, of equal width (at least 8).
+void radix_plan(int nbits, int* passes, int* bits) {
+  if (nbits <= 0) {
+    *passes = 0;
+    *bits = 8;
+    return;
+  }
+  int p = (nbits + kMaxDigitBits - 1) / kMaxDigitBits;
+  int b = (nbits + p - 1) / p;
+  if (b < 8) {
+    b = 8;
+    p = (nbits + 7) / 8;
+  }
+  *passes = p;
+  *bits = b;
+}
+int radix_passes(int nbits) {
+  int p, b;
+  radix_plan(nbits, &p, &b);
+  return p;
+}
+
+// Digit-count scratch of a sort of n pairs (int32 entries): enough for every
+// digit width.
+int64_t radix_scratch_entries(int64_t n) {
+  return 2 * ((int64_t)1 << kMaxDigitBits) * ((n + kSortTile - 1) / kSortTile);
+}
+
 // Stable LSD radix sort of (key, val) pairs by bits [lo_bit, hi_bit), digits
-// from lo_bit up (the order of keys equal in those bits is kept).  The result
-// is left in (k0, v0) or (k1, v1); *in_alt tells which.
+// from lo_bit up (the order of keys equal in those bits is kept), in the
+// passes of radix_plan.  The result is left in (k0, v0) or (k1, v1); *in_alt
+// tells which.  `scratch` (radix_scratch_entries(n) entries) may be null: the
+// sort then allocates its own.
 cudaError_t radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
-                       int lo_bit, int hi_bit, cudaStream_t s, bool* in_alt) {
+                       int lo_bit, int hi_bit, cudaStream_t s, bool* in_alt,
+                       int32_t* scratch = nullptr) {
   *in_alt = false;
   const int nbits = hi_bit - lo_bit;
   if (n <= 1 || nbits <= 0) return cudaSuccess;
+  int passes, bits;
+  radix_plan(nbits, &passes, &bits);
   const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-  int32_t* cnt = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&cnt),
-                                  sizeof(int32_t) * 2 * kDigits * ntiles, s);
-  if (e != cudaSuccess) return e;
-  int32_t* lcnt = cnt + kDigits * ntiles;
-  e = ensure_dynamic_smem(reinterpret_cast<const void*>(radix_scatter), kScatterSmem);
-  const int passes = (nbits + 7) / 8;
+  int32_t* cnt = scratch;
+  cudaError_t e = cudaSuccess;
+  if (!cnt) {
+    e = cudaMallocAsync(reinterpret_cast<void**>(&cnt), sizeof(int32_t) * radix_scratch_entries(n), s);
+    if (e != cudaSuccess) return e;
+  }
   uint64_t *ki = k0, *ko = k1;
   uint32_t *vi = v0, *vo = v1;
   for (int pass = 0; pass < passes && e == cudaSuccess; ++pass) {
-    const int shift = lo_bit + 8 * pass;
-    radix_hist<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n, shift, cnt, lcnt, ntiles); DF_COUNT();
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = exclusive_scan_i32(cnt, cnt, kDigits * ntiles, s);
-    if (e == cudaSuccess) {
-      radix_scatter<<<(unsigned)ntiles, kSortThreads, kScatterSmem, s>>>(ki, vi, ko, vo, n, shift, cnt,
-                                                                          lcnt, ntiles); DF_COUNT();
-      e = cudaGetLastError();
-    }
+    const int shift = lo_bit + bits * pass;
+    e = (bits == 8) ? radix_pass<8>(ki, vi, ko, vo, n, shift, hi_bit, cnt, ntiles, s)
+                    : radix_pass<9>(ki, vi, ko, vo, n, shift, hi_bit, cnt, ntiles, s);
     std::swap(ki, ko);
     std::swap(vi, vo);
     *in_alt = !*in_alt;
   }
-  cudaError_t e2 = cudaFreeAsync(cnt, s);
+  cudaError_t e2 = scratch ? cudaSuccess : cudaFreeAsync(cnt, s);
   return e != cudaSuccess ? e : e2;
 }
 
@@ -502,7 +577,7 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
 
   uint64_t *k0 = nullptr, *k1 = nullptr;
   uint32_t *v0 = nullptr, *v1 = nullptr;
-  int32_t *head = nullptr, *fid = nullptr;
+  int32_t *head = nullptr, *fid = nullptr, *sort_cnt = nullptr;
   const size_t nn = (size_t)std::max<int64_t>(n, 1);
   cudaError_t e = cudaSuccess;
   auto cleanup = [&]() {
@@ -512,6 +587,7 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
     if (v1) cudaFreeAsync(v1, s);
     if (head) cudaFreeAsync(head, s);
     if (fid) cudaFreeAsync(fid, s);
+    if (sort_cnt) cudaFreeAsync(sort_cnt, s);
   };
   if (n > 0) {
     e = cudaMallocAsync(reinterpret_cast<void**>(&k0), sizeof(uint64_t) * nn, s);
@@ -520,6 +596,8 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&v1), sizeof(uint32_t) * nn, s);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&head), sizeof(int32_t) * nn, s);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&fid), sizeof(int32_t) * nn, s);
+    if (e == cudaSuccess)
+      e = cudaMallocAsync(reinterpret_cast<void**>(&sort_cnt), sizeof(int32_t) * radix_scratch_entries(n), s);
     if (e != cudaSuccess) {
       cleanup();
       cudaGetLastError();
@@ -529,16 +607,15 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
   }
 
   // Mode order of the sorts (the chain of the header): the start is the mode
-  // that minimises the total number of 8-bit digit passes; with 64-bit keys
-  // every start costs the same full sort, and each later mode sorts its o
-  // bits only.
+  // that minimises the total number of digit passes; with 64-bit keys every
+  // start costs the same full sort, and each later mode sorts its o bits only.
   int bits[3];
   for (int a = 0; a < 3; ++a) bits[a] = nbits_for(h->dims[a]);
   const bool narrow = bits[0] + bits[1] + bits[2] <= 64;
-  auto o_passes = [&](int m) { return (bits[m] + 7) / 8; };
+  auto o_passes = [&](int m) { return radix_passes(bits[m]); };
   auto full_passes = [&](int m) {
     const int bo = bits[m], bf = bits[(m + 2) % 3], bi = bits[(m + 1) % 3];
-    return narrow ? (bo + bf + bi + 7) / 8 : (bi + 7) / 8 + (bo + bf + 7) / 8;
+    return narrow ? radix_passes(bo + bf + bi) : radix_passes(bi) + radix_passes(bo + bf);
   };
   int start = 2, best = 1 << 30;
   for (int m = 2; m >= 0; --m) {
@@ -599,13 +676,13 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
       make_keys64_val<<<grid_for(n), 256, 0, s>>>(d_idx, d_val, n, M.o, M.f, M.in, bf, bi, kin, vin);
       DF_COUNT();
       e = cudaGetLastError();
-      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, 0, bo + bf + bi, s, &alt);
+      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, 0, bo + bf + bi, s, &alt, sort_cnt);
     } else if (narrow) {
       // the previous order ascends in this mode's (f, in): sort the o bits
       rotate_keys<<<grid_for(n), 256, 0, s>>>(kin, n, prev_bo, prev_bf, prev_bi);
       DF_COUNT();
       e = cudaGetLastError();
-      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, bf + bi, bo + bf + bi, s, &alt);
+      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, bf + bi, bo + bf + bi, s, &alt, sort_cnt);
     } else if (chained) {
       // previous payload = COO positions in an order ascending in this mode's
       // (f, in): key (o, f), sort the o bits
@@ -614,11 +691,11 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
       e = cudaGetLastError();
       std::swap(kin, kalt);
       std::swap(vin, valt);
-      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, bf, bo + bf, s, &alt);
+      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, bf, bo + bf, s, &alt, sort_cnt);
     } else {
       make_keys_in<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.in, kin, vin); DF_COUNT();
       e = cudaGetLastError();
-      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, 0, bi, s, &alt);
+      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, 0, bi, s, &alt, sort_cnt);
       if (alt) {
         std::swap(kin, kalt);
         std::swap(vin, valt);
@@ -627,7 +704,7 @@ dfacto_status build_modes(dfacto_t* h, const int32_t* d_idx, const float* d_val)
         make_keys_of<<<grid_for(n), 256, 0, s>>>(d_idx, n, M.o, M.f, bf, vin, kin); DF_COUNT();
         e = cudaGetLastError();
       }
-      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, 0, bo + bf, s, &alt2);
+      if (e == cudaSuccess) e = radix_sort(kin, vin, kalt, valt, n, 0, bo + bf, s, &alt2, sort_cnt);
       alt = alt2;
     }
     if (e != cudaSuccess) {
