@@ -146,18 +146,21 @@ __global__ void make_keys_chain(const int32_t* __restrict__ idx, int64_t nnz, in
 // into output offsets afterwards), and tile-major: lcnt[tile * D + d] (kept
 // for the tile's own digit order in radix_scatter).  A digit is BITS bits of
 // the key from `shift`, masked by dmask (the last digit of a range may be
-// narrower).
+// narrower).  Each warp counts into its own counters: one add of 32 when the
+// warp's 32 digits are equal (the high digits of power-law indices), else one
+// shared-memory atomic per lane; the warps' counters are added at the end.
 template <int BITS>
 __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __restrict__ key,
                                                           int64_t n, int shift, uint32_t dmask,
                                                           int32_t* __restrict__ cnt,
                                                           int32_t* __restrict__ lcnt, int64_t ntiles) {
   constexpr int D = 1 << BITS;
-  __shared__ int32_t s_cnt[D];
-  for (int d = threadIdx.x; d < D; d += kSortThreads) s_cnt[d] = 0;
-  __syncthreads();
+  constexpr int W = kSortThreads / 32;
+  __shared__ int32_t s_cnt[W][D];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = lane; d < D; d += 32) s_cnt[warp][d] = 0;
+  __syncwarp();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  const int lane = threadIdx.x & 31;
   // all of the thread's keys first (independent loads in flight together)
   int dg[kSortRounds];
 #pragma unroll
@@ -168,13 +171,21 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint64_t* __res
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const int d = dg[r];
-    const unsigned peers = __match_any_sync(kFull, d);
-    if (d < D && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[d], __popc(peers));
+    const int d0 = __shfl_sync(kFull, d, 0);
+    if (__all_sync(kFull, d == d0)) {
+      if (lane == 0 && d0 < D) s_cnt[warp][d0] += 32;
+    } else if (d < D) {
+      atomicAdd(&s_cnt[warp][d], 1);
+    }
+    __syncwarp();
   }
   __syncthreads();
   for (int d = threadIdx.x; d < D; d += kSortThreads) {
-    cnt[(int64_t)d * ntiles + blockIdx.x] = s_cnt[d];
-    lcnt[(int64_t)blockIdx.x * D + d] = s_cnt[d];
+    int32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) c += s_cnt[w][d];
+    cnt[(int64_t)d * ntiles + blockIdx.x] = c;
+    lcnt[(int64_t)blockIdx.x * D + d] = c;
   }
 }
 
