@@ -401,7 +401,9 @@ __global__ void row_pointers(const int32_t* __restrict__ fiber_row, int64_t nfib
   }
 }
 
-// end_bits: bit e set for the last nonzero e of every fiber.
+// end_bits: bit e set for the last nonzero e of every fiber, from nz_ptr (the
+// batched tensors' concatenated copies; a tensor's own build sets the bits in
+// segment_flags).
 __global__ void fiber_end_bits(const int64_t* __restrict__ nz_ptr, int64_t nfib,
                                uint32_t* __restrict__ bits) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
