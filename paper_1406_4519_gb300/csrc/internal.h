@@ -109,9 +109,16 @@ struct dfacto_handle {
   int32_t* flags = nullptr;                   // [kNumFlags]
   double* partials = nullptr;                 // reduction partials
   int64_t partials_cap = 0;                   // doubles
-  float* carry = nullptr;                     // MTTKRP CTA carries [ncta x 2 x R]
+  float* carry = nullptr;                     // MTTKRP CTA carries [ncta x 2 x walk rank]
   int32_t* carry_row = nullptr;               // [ncta x 4] head row, tail row, slot info
   int64_t carry_cap = 0;                      // CTAs
+  int carry_rank = 0;                         // columns of a carry row the buffer holds
+  // MTTKRP at a rank that is not a multiple of four: the two gathered factors
+  // and the output as zero-padded FP32 rows of a multiple of four columns
+  // [max dim x padded rank] each (lazy)
+  float* pad_in = nullptr;
+  float* pad_f = nullptr;
+  float* pad_out = nullptr;
   double* host_scal = nullptr;                // host mirror of scal
   int32_t* host_flags = nullptr;              // host mirror of flags
   int64_t bytes = 0;
@@ -165,6 +172,10 @@ dfacto_status ensure_segments(dfacto_t* h, int mode);
 
 // ---- MTTKRP (mttkrp*.cu) --------------------------------------------------
 WalkCfg choose_walk(int R, int dtype, int64_t nnz, int64_t nfib, int seg_opt, int vec_opt);
+// Rank the MTTKRP walk runs at: R, or R rounded up to a multiple of four (the
+// factors then gathered from zero-padded FP32 copies) when R > 2 is not one
+// and no lane width was asked for.
+int walk_rank(int R, int vec_opt);
 dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out);
 
 // ---- batches (batch.cu, dense.cu) -----------------------------------------
