@@ -439,12 +439,18 @@ dfacto_status dual_pass(dfacto_t* h) {
   dfacto_status st = ensure_segments(h, 0);
   if (st != DFACTO_OK) return st;
   // The mode-1 walk's segments; dual_walk2 keeps five accumulators and two
-  // gathered rows per lane, so its lanes take at most four columns.
-  WalkCfg cfg = M.cfg;
+  // gathered rows per lane, so its lanes take at most four columns.  At a rank
+  // that is not a multiple of four it walks zero-padded FP32 copies of the
+  // factors and gradients at the rank rounded up, as the MTTKRP does (the zero
+  // columns add nothing to the four terms).
+  const int R = h->R;
+  const int RP = (M.cfg.kernel == 2) ? walk_rank(R, h->opt.vec) : R;
+  const bool padded = RP != R;
+  WalkCfg cfg = padded ? choose_walk(RP, DFACTO_F32, h->nnz, M.nfib, h->opt.seg_nnz, 0) : M.cfg;
   if (cfg.kernel == 2 && cfg.vec > 4) {
     cfg.vec = 4;
     int G = 1;
-    while (G * 4 < h->R) G <<= 1;
+    while (G * 4 < RP) G <<= 1;
     cfg.G = G;
   }
   const int segs = kWalkWarps * (32 / cfg.G);
@@ -465,6 +471,24 @@ dfacto_status dual_pass(dfacto_t* h) {
     DF_CUDA(h, cudaMemsetAsync(h->scal + kT110, 0, 4 * sizeof(double), h->stream));
     return DFACTO_OK;
   }
+  const void* Fm[3] = {h->F[0], h->F[1], h->F[2]};
+  const float* Gm[3] = {h->grad[0], h->grad[1], h->grad[2]};
+  if (padded) {
+    const int64_t rows = (int64_t)h->dims[0] + h->dims[1] + h->dims[2];
+    if (!h->pad_dual &&
+        (st = dalloc(h, (void**)&h->pad_dual, sizeof(float) * 2 * (size_t)rows * RP)) != DFACTO_OK)
+      return st;
+    float* q = h->pad_dual;
+    for (int m = 0; m < 3; ++m) {
+      float* pf = q;
+      float* pg = q + (size_t)h->dims[m] * RP;
+      DF_CUDA(h, pad_factor_rows(h->F[m], h->dtype, h->dims[m], R, RP, pf, h->stream));
+      DF_CUDA(h, pad_factor_rows(h->grad[m], DFACTO_F32, h->dims[m], R, RP, pg, h->stream));
+      Fm[m] = pf;
+      Gm[m] = pg;
+      q += 2 * (size_t)h->dims[m] * RP;
+    }
+  }
   DualParams a;
   a.fiber_idx = M.fiber_idx;
   a.fiber_row = M.fiber_row;
@@ -473,19 +497,19 @@ dfacto_status dual_pass(dfacto_t* h) {
   a.nz_val = M.nz_val;
   a.seg_fib = M.seg_fib;
   a.end_bits = M.end_bits;
-  a.A = h->F[0];
-  a.B = h->F[1];
-  a.C = h->F[2];
-  a.GA = h->grad[0];
-  a.GB = h->grad[1];
-  a.GC = h->grad[2];
+  a.A = Fm[0];
+  a.B = Fm[1];
+  a.C = Fm[2];
+  a.GA = Gm[0];
+  a.GB = Gm[1];
+  a.GC = Gm[2];
   a.gscale = gscale;
   a.part = h->partials;
   a.nnz = h->nnz;
   a.nfib = M.nfib;
-  a.R = h->R;
+  a.R = RP;
   a.seg = cfg.seg;
-  cudaError_t e = (h->dtype == DFACTO_BF16)
+  cudaError_t e = (h->dtype == DFACTO_BF16 && !padded)
                       ? launch<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, h->stream, cfg.kernel)
                       : launch<float>(cfg.vec, cfg.G, a, ncta, h->stream, cfg.kernel);
   if (e != cudaSuccess) return cuda_fail(h, e, "dual_walk launch");

@@ -119,6 +119,9 @@ struct dfacto_handle {
   float* pad_in = nullptr;
   float* pad_f = nullptr;
   float* pad_out = nullptr;
+  // the line search's trilinear pass at such a rank: A, B, C and their
+  // gradients as padded FP32 rows [(dims[0] + dims[1] + dims[2]) x padded rank x 2] (lazy)
+  float* pad_dual = nullptr;
   double* host_scal = nullptr;                // host mirror of scal
   int32_t* host_flags = nullptr;              // host mirror of flags
   int64_t bytes = 0;
@@ -176,6 +179,9 @@ WalkCfg choose_walk(int R, int dtype, int64_t nnz, int64_t nfib, int seg_opt, in
 // factors then gathered from zero-padded FP32 copies) when R > 2 is not one
 // and no lane width was asked for.
 int walk_rank(int R, int vec_opt);
+// dst[r, c] = src[r, c] for c < R, 0 for R <= c < RP (FP32 rows of RP columns).
+cudaError_t pad_factor_rows(const void* src, int src_dtype, int64_t rows, int R, int RP, float* dst,
+                            cudaStream_t s);
 dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out);
 
 // ---- batches (batch.cu, dense.cu) -----------------------------------------

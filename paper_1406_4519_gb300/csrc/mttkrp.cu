@@ -136,6 +136,18 @@ int walk_rank(int R, int vec_opt) {
   return (vec_opt == 0 && R > 2 && R % 4 != 0) ? (R + 3) / 4 * 4 : R;
 }
 
+cudaError_t pad_factor_rows(const void* src, int src_dtype, int64_t rows, int R, int RP, float* dst,
+                            cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  if (src_dtype == DFACTO_BF16)
+    pad_rows<__nv_bfloat16><<<rows_grid(rows * RP), 256, 0, s>>>(static_cast<const __nv_bfloat16*>(src),
+                                                                   rows, R, RP, dst);
+  else
+    pad_rows<float><<<rows_grid(rows * RP), 256, 0, s>>>(static_cast<const float*>(src), rows, R, RP, dst);
+  DF_COUNT();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mttkrp_fixup(const int32_t* carry_row, const float* carry,
                                 const int64_t* fiber_ptr, const int64_t* nz_ptr, float* out, int R,
                                 int64_t P, int64_t ncta, int64_t dim_o, int32_t* bad,
@@ -218,23 +230,8 @@ dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out) {
     const size_t bytes = sizeof(float) * (size_t)maxdim * RP;
     for (float** q : {&h->pad_in, &h->pad_f, &h->pad_out})
       if (!*q && (st = dalloc(h, reinterpret_cast<void**>(q), bytes)) != DFACTO_OK) return st;
-    const int64_t din = h->dims[M.in], df = h->dims[M.f];
-    if (h->dtype == DFACTO_BF16) {
-      pad_rows<__nv_bfloat16><<<rows_grid(din * RP), 256, 0, h->stream>>>(
-          static_cast<const __nv_bfloat16*>(Fin), din, R, RP, h->pad_in);
-      DF_COUNT();
-      pad_rows<__nv_bfloat16><<<rows_grid(df * RP), 256, 0, h->stream>>>(
-          static_cast<const __nv_bfloat16*>(Ff), df, R, RP, h->pad_f);
-      DF_COUNT();
-    } else {
-      pad_rows<float><<<rows_grid(din * RP), 256, 0, h->stream>>>(static_cast<const float*>(Fin), din, R,
-                                                                    RP, h->pad_in);
-      DF_COUNT();
-      pad_rows<float><<<rows_grid(df * RP), 256, 0, h->stream>>>(static_cast<const float*>(Ff), df, R,
-                                                                   RP, h->pad_f);
-      DF_COUNT();
-    }
-    DF_CUDA(h, cudaGetLastError());
+    DF_CUDA(h, pad_factor_rows(Fin, h->dtype, h->dims[M.in], R, RP, h->pad_in, h->stream));
+    DF_CUDA(h, pad_factor_rows(Ff, h->dtype, h->dims[M.f], R, RP, h->pad_f, h->stream));
     Fin = h->pad_in;
     Ff = h->pad_f;
     wout = h->pad_out;

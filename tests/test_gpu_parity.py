@@ -261,6 +261,29 @@ def test_mttkrp_bf16_factors(R, walk):
         assert rel(got, oracle.mttkrp(ot, mode, Fbf)) <= MTTKRP_TOL
 
 
+@pytest.mark.parametrize("dtype", [dfacto.F32, dfacto.BF16])
+def test_mttkrp_padded_ranks(dtype):
+    """Ranks that are not a multiple of four walk zero-padded FP32 copies of the
+    factors at the rank rounded up (the default lane width); the result, copied
+    back to R columns, is the oracle's within the MTTKRP bar for every such rank
+    from 3 to 31, on power-law rows that span many CTAs (small segments), and
+    so is the unpadded walk that an explicit lane width keeps."""
+    dims = [900, 700, 500]
+    idx, val = synth.zipf_tensor(dims, 80000, [1.2, 1.1, 1.3], seed=77, device="cuda",
+                                 values="uniform")
+    ot = as_oracle(idx, val, dims)
+    for R in (3, 5, 6, 7, 9, 10, 11, 13, 14, 15, 18, 22, 31):
+        F = synth.normal_factors(dims, R, seed=100 + R, device="cuda")
+        Fh = [host(f.to(torch.bfloat16)) if dtype == dfacto.BF16 else host(f) for f in F]
+        for vec in (0, 1):
+            t = dfacto.Tensor(idx, val, dims, rank=R, factor_dtype=dtype, seg_nnz=64, vec=vec)
+            t.set_factors(F)
+            for mode in range(3):
+                got = host(t.mttkrp(mode))
+                assert got.shape == (dims[mode], R)
+                assert rel(got, oracle.mttkrp(ot, mode, Fh)) <= MTTKRP_TOL, (R, vec, mode)
+
+
 # ---------------------------------------------------------------------------
 # ALS, fit and GD (step-wise: the oracle starts from the GPU's state).
 # ---------------------------------------------------------------------------
