@@ -564,6 +564,50 @@ def test_gd_stepwise(lam_reg, R):
         alpha_prev = alpha
 
 
+@pytest.mark.parametrize("R", [36, 128])
+def test_large_ranks_mttkrp_als_gd(R):
+    """Ranks above 32 (up to the largest accepted, 128) take the generic row
+    solve and store, four columns per lane in the merges and the fix-up, and an
+    R x R Gamma of up to 128 x 128: the MTTKRP of every mode is the oracle's
+    within the MTTKRP bar, a regularized ALS sweep from the GPU's state agrees
+    with the oracle's to 1e-4 normwise, and two GD steps agree as in the
+    step-wise GD test (same accepted alpha, objective within ray_tolerance,
+    factors to 1e-5)."""
+    dims = [300, 250, 200]
+    lam = 1.0
+    idx, val = synth.zipf_tensor(dims, 20000, [1.2, 1.1, 1.3], seed=900 + R, device="cuda",
+                                 values="uniform")
+    F = synth.normal_factors(dims, R, seed=901 + R, device="cuda")
+    ot = as_oracle(idx, val, dims)
+    t = dfacto.Tensor(idx, val, dims, rank=R, lambda_reg=lam)
+    t.set_factors(F)
+    Fh = [host(f) for f in F]
+    for mode in range(3):
+        assert rel(host(t.mttkrp(mode)), oracle.mttkrp(ot, mode, Fh)) <= MTTKRP_TOL, mode
+    before = [host(f) for f in t.factors()]
+    st, fit = t.als_iter()
+    assert st in (dfacto.OK, dfacto.ESINGULAR)
+    st_o, Fo, lam_o, fit_o = oracle.als_sweep(ot, before, lam)
+    after = [host(f) for f in t.factors()]
+    for m in range(3):
+        assert rel(after[m], Fo[m]) <= 1e-4, m
+    g = dfacto.Tensor(idx, val, dims, rank=R, lambda_reg=lam)
+    g.set_factors(F)
+    alpha_prev = 0.0
+    for it in range(2):
+        before = [host(f) for f in g.factors()]
+        st, loss, alpha = g.gd_iter()
+        st_o, Fo, alpha_o, loss_o, g2 = oracle.gd_step(ot, before, alpha_prev, lam)
+        assert st == dfacto.OK and st_o == oracle.OK
+        assert alpha == alpha_o, (it, alpha, alpha_o)
+        G = oracle.gd_gradient(ot, before, lam)
+        assert abs(loss - loss_o) <= ray_tolerance(ot, before, G, alpha_o, lam), (it, loss, loss_o)
+        after = [host(f) for f in g.factors()]
+        for m in range(3):
+            assert rel(after[m], Fo[m]) <= 1e-5, (it, m)
+        alpha_prev = alpha
+
+
 # ---------------------------------------------------------------------------
 # Error paths on the device.
 # ---------------------------------------------------------------------------
