@@ -71,7 +71,12 @@ typedef enum dfacto_dtype {
  *                 most 4096; 0 lets the library choose.  Rounded to a multiple
  *                 of 32.
  *   vec           factor columns per lane in the MTTKRP kernel (1, 2, 4 or 8;
- *                 must divide R); 0 lets the library choose.
+ *                 must divide R); 0 lets the library choose.  With 0, at a rank
+ *                 R > 2 that is not a multiple of 4, the MTTKRP and the GD line
+ *                 search gather from zero-padded FP32 copies of the factors at
+ *                 R rounded up to a multiple of 4 (16-byte gathers; the result
+ *                 is the same sums up to their order), which the handle
+ *                 allocates on first use.
  *   walk          MTTKRP kernel: 1 detects fiber ends from the fiber pointers
  *                 as it walks, 2 from a per-nonzero end bitmask and closes the
  *                 fibers of a few steps together; 0 lets the library choose.

@@ -444,9 +444,13 @@ dfacto_status dual_pass(dfacto_t* h) {
   // factors and gradients at the rank rounded up, as the MTTKRP does (the zero
   // columns add nothing to the four terms).
   const int R = h->R;
-  const int RP = (M.cfg.kernel == 2) ? walk_rank(R, h->opt.vec) : R;
+  const int RP = walk_rank(R, h->opt.vec);
   const bool padded = RP != R;
-  WalkCfg cfg = padded ? choose_walk(RP, DFACTO_F32, h->nnz, M.nfib, h->opt.seg_nnz, 0) : M.cfg;
+  WalkCfg cfg = M.cfg;
+  if (padded) {
+    cfg = choose_walk(RP, DFACTO_F32, h->nnz, M.nfib, h->opt.seg_nnz, 0);
+    cfg.kernel = M.cfg.kernel;
+  }
   if (cfg.kernel == 2 && cfg.vec > 4) {
     cfg.vec = 4;
     int G = 1;

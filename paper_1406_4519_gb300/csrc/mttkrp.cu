@@ -196,11 +196,16 @@ dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out) {
   // copies of the two gathered factors at the padded rank RP (one 16-byte
   // gather per lane: R = 10 walks 3 of 4 lanes per group instead of 5 of 8
   // with 8-byte gathers, measured 1.45x faster) and its output is copied back
-  // to R columns; an explicit lane width keeps the unpadded walk.
+  // to R columns; an explicit lane width keeps the unpadded walk.  Both walks
+  // pad alike, so they still compute the same sums in the same order.
   const int R = h->R;
-  const int RP = (M.cfg.kernel == 2) ? walk_rank(R, h->opt.vec) : R;
+  const int RP = walk_rank(R, h->opt.vec);
   const bool padded = RP != R;
-  const WalkCfg cfg = padded ? choose_walk(RP, DFACTO_F32, h->nnz, M.nfib, h->opt.seg_nnz, 0) : M.cfg;
+  WalkCfg cfg = M.cfg;
+  if (padded) {
+    cfg = choose_walk(RP, DFACTO_F32, h->nnz, M.nfib, h->opt.seg_nnz, 0);
+    cfg.kernel = M.cfg.kernel;
+  }
   dfacto_status st = ensure_segments(h, mode);
   if (st != DFACTO_OK) return st;
   const int segs = kWalkWarps * (32 / cfg.G);
@@ -262,7 +267,7 @@ dfacto_status mttkrp_launch(dfacto_t* h, int mode, float* out) {
       e = (h->dtype == DFACTO_BF16 && !padded) ? launch_walk2<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, h->stream)
                                                : launch_walk2<float>(cfg.vec, cfg.G, a, ncta, h->stream);
     else
-      e = (h->dtype == DFACTO_BF16)
+      e = (h->dtype == DFACTO_BF16 && !padded)
               ? launch_walk<__nv_bfloat16>(cfg.vec, cfg.G, a, ncta, smem, h->stream)
               : launch_walk<float>(cfg.vec, cfg.G, a, ncta, smem, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "mttkrp_walk launch");

@@ -229,10 +229,13 @@ def test_mttkrp_empty_tensor_and_empty_rows():
     np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-6)
 
 
-def test_mttkrp_is_bitwise_deterministic():
+@pytest.mark.parametrize("R", [32, 10])
+def test_mttkrp_is_bitwise_deterministic(R):
+    """Repeated calls give the same bits, and so do the two walks (at R = 10
+    both run on the padded copies)."""
     dims = [2000, 1000, 500]
-    t, idx, val, F = make(dims, 200000, 32, seed=400, seg=32, zipf=[1.2, 1.2, 1.2], walk=1)
-    t2 = dfacto.Tensor(idx, val, dims, rank=32, seg_nnz=32, walk=2)
+    t, idx, val, F = make(dims, 200000, R, seed=400, seg=32, zipf=[1.2, 1.2, 1.2], walk=1)
+    t2 = dfacto.Tensor(idx, val, dims, rank=R, seg_nnz=32, walk=2)
     t2.set_factors(F)
     for mode in range(3):
         a = t.mttkrp(mode).clone()
