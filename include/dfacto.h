@@ -115,7 +115,8 @@ typedef struct dfacto_info {
   double norm_x2;        /* ||X||^2 in FP64                                    */
   int32_t factor_dtype;
   int32_t seg_nnz[3];    /* MTTKRP segment length in use per mode              */
-  int32_t vec[3];        /* MTTKRP columns per lane in use per mode            */
+  int32_t vec[3];        /* MTTKRP columns per lane in use per mode (of the
+                            padded FP32 copies at a padded rank, see vec)       */
 } dfacto_info;
 
 /*

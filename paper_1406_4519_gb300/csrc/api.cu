@@ -397,10 +397,13 @@ dfacto_status dfacto_get_info(dfacto_t* h, dfacto_info* info) {
   std::memcpy(info->dims, h->dims, sizeof(h->dims));
   info->rank = h->R;
   info->nnz = h->nnz;
+  const int RP = walk_rank(h->R, h->opt.vec);
   for (int m = 0; m < 3; ++m) {
     info->nfib[m] = h->m[m].nfib;
     info->seg_nnz[m] = h->m[m].cfg.seg;
-    info->vec[m] = h->m[m].cfg.vec;
+    info->vec[m] = (RP != h->R)
+                       ? choose_walk(RP, DFACTO_F32, h->nnz, h->m[m].nfib, h->opt.seg_nnz, 0).vec
+                       : h->m[m].cfg.vec;
   }
   info->device_bytes = h->bytes;
   info->factor_dtype = h->dtype;

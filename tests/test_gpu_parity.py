@@ -281,6 +281,8 @@ def test_mttkrp_padded_ranks(dtype):
         for vec in (0, 1):
             t = dfacto.Tensor(idx, val, dims, rank=R, factor_dtype=dtype, seg_nnz=64, vec=vec)
             t.set_factors(F)
+            # the lane width in use: four columns of the padded copies, or the one asked for
+            assert list(t.info().vec) == [4 if vec == 0 else 1] * 3, (R, vec)
             for mode in range(3):
                 got = host(t.mttkrp(mode))
                 assert got.shape == (dims[mode], R)
