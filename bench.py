@@ -603,7 +603,7 @@ def run_ours(args, rank, world, local_rank):
         val_h = val.cpu().pin_memory()
         F0_h = [f.cpu().pin_memory() for f in F0]
         Fout_h = [torch.empty(d, R, dtype=torch.float32).pin_memory() for d in dims]
-        n_e2e = max(1, min(args.steps, 10))
+        n_e2e = max(1, min(args.steps, 30))
 
         def e2e_step():
             h = dfacto.Tensor(idx_h, val_h, dims, rank=R, factor_dtype=dtype, stream=stream)
