@@ -258,7 +258,8 @@ void dfacto_destroy(dfacto_t* h) {
   for (void* q : {(void*)h->N, (void*)h->Fh, (void*)h->lambda, (void*)h->inv_lambda, (void*)h->ipart,
                   (void*)h->gd_mats, (void*)h->gd_scratch, (void*)h->W, (void*)h->rr_work, (void*)h->W32, (void*)h->scal,
                   (void*)h->flags, (void*)h->partials, (void*)h->carry, (void*)h->carry_row,
-                  (void*)h->pad_in, (void*)h->pad_f, (void*)h->pad_out, (void*)h->pad_dual})
+                  (void*)h->pad_in, (void*)h->pad_f, (void*)h->pad_out, (void*)h->pad_dual,
+                  (void*)h->ls_vals})
     if (q) cudaFreeAsync(q, h->stream);
   delete[] h->host_scal;
   delete[] h->host_flags;

@@ -832,27 +832,27 @@ __device__ int poly_roots(const double* c, int n, double lo, double hi, double* 
   return nr;
 }
 
-// One CTA.  exact == 0: backtracking as specified in dfacto.h.  exact == 1:
-// the exact minimiser over alpha > 0 -- the coefficients of f are formed in
-// FP64 from the same terms, the real roots of f' on (0, B] (B: Fujiwara's
-// bound on the roots of f') are isolated, the local minima among them are
-// evaluated in the factored form above, and the smallest is taken when it
-// lowers f; when there is none (possible only through rounding of a
-// degenerate ray), the step falls back to backtracking.
-// The joint model of Appendix F weights the tensor term by mu and adds the
-// ratings term, a quartic in alpha with coefficients ycoef[0..4] (nullable).
-__global__ void __launch_bounds__(256) gd_line_search(const double* __restrict__ mats, int R,
-                                                     double lambda_reg, double* __restrict__ scal,
-                                                     int32_t* __restrict__ lsfail, int exact,
-                                                     double mu, const double* __restrict__ ycoef) {
-  __shared__ double red[256];
-  __shared__ double s_q;
-  __shared__ double s_qc[256][7];
-  __shared__ double s_cand[kPolyMax];
-  __shared__ int s_ncand;
-  const int tid = threadIdx.x;
-  const int RR = R * R;
-  auto Q = [&](double a) {
+// f(alpha) of the search ray, evaluated by a whole block of 256 threads (the
+// model term Q block-reduced in a fixed order); every caller gets the same bits
+// for the same alpha.
+struct RayObjective {
+  const double* mats;
+  int R;
+  double lambda_reg, mu;
+  const double* ycoef;
+  double nx2, t0, t1, t2, t3;
+  __device__ RayObjective(const double* m, int r, double lam, const double* __restrict__ scal, double mu_,
+                          const double* yc)
+      : mats(m), R(r), lambda_reg(lam), mu(mu_), ycoef(yc) {
+    nx2 = scal[kNormX2];
+    t0 = scal[kT000];
+    t1 = scal[kT100] + scal[kT010] + scal[kT001];
+    t2 = scal[kT110] + scal[kT101] + scal[kT011];
+    t3 = scal[kT111];
+  }
+  // called by all threads of the block; red: [blockDim.x] shared doubles
+  __device__ double Q(double a, double* red, double* s_q) const {
+    const int tid = threadIdx.x, RR = R * R;
     double s = 0.0;
     for (int e = tid; e < RR; e += blockDim.x) {
       double p = 1.0;
@@ -867,12 +867,13 @@ __global__ void __launch_bounds__(256) gd_line_search(const double* __restrict__
     if (tid == 0) {
       double t = 0.0;
       for (int i = 0; i < (int)blockDim.x; ++i) t += red[i];
-      s_q = t;
+      *s_q = t;
     }
     __syncthreads();
-    return s_q;
-  };
-  auto trace_sum = [&](double a) {
+    return *s_q;
+  }
+  __device__ double trace_sum(double a) const {
+    const int RR = R * R;
     double t = 0.0;
     for (int n = 0; n < 3; ++n) {
       const double* P = mats + (size_t)n * 3 * RR;
@@ -882,20 +883,62 @@ __global__ void __launch_bounds__(256) gd_line_search(const double* __restrict__
       }
     }
     return t;
-  };
-  const double nx2 = scal[kNormX2];
-  const double t0 = scal[kT000];
-  const double t1 = scal[kT100] + scal[kT010] + scal[kT001];
-  const double t2 = scal[kT110] + scal[kT101] + scal[kT011];
-  const double t3 = scal[kT111];
-  auto f = [&](double a) {
+  }
+  __device__ double f(double a, double* red, double* s_q) const {
     const double P = t0 - a * t1 + a * a * t2 - a * a * a * t3;
-    double v = 0.5 * mu * (nx2 - 2.0 * P + Q(a));
+    double v = 0.5 * mu * (nx2 - 2.0 * P + Q(a, red, s_q));
     if (lambda_reg != 0.0) v += 0.5 * lambda_reg * trace_sum(a);
     if (ycoef) v += ycoef[0] + a * (ycoef[1] + a * (ycoef[2] + a * (ycoef[3] + a * ycoef[4])));
     return v;
-  };
-  const double f0 = f(0.0);
+  }
+};
+
+// The backtracking trials all at once: block 0 evaluates f(0), block 1 + t the
+// t-th trial step alpha0 / 2^t (alpha0 = min(2 alpha_prev, 1), or 1 at the
+// first step), each as the single-block search would; fvals[1 + kLineSearchTrials].
+__global__ void __launch_bounds__(256) gd_ray_values(const double* __restrict__ mats, int R,
+                                                    double lambda_reg, const double* __restrict__ scal,
+                                                    double mu, const double* __restrict__ ycoef,
+                                                    double* __restrict__ fvals) {
+  __shared__ double red[256];
+  __shared__ double s_q;
+  const RayObjective obj(mats, R, lambda_reg, scal, mu, ycoef);
+  double a = 0.0;
+  if (blockIdx.x > 0) {
+    const double prev = scal[kAlpha];
+    const double a0 = prev > 0.0 ? fmin(2.0 * prev, 1.0) : 1.0;
+    a = ldexp(a0, -(int)(blockIdx.x - 1));  // exact: the halvings of the sequential search
+  }
+  const double v = obj.f(a, red, &s_q);
+  if (threadIdx.x == 0) fvals[blockIdx.x] = v;
+}
+
+// One CTA.  exact == 0: backtracking as specified in dfacto.h.  exact == 1:
+// the exact minimiser over alpha > 0 -- the coefficients of f are formed in
+// FP64 from the same terms, the real roots of f' on (0, B] (B: Fujiwara's
+// bound on the roots of f') are isolated, the local minima among them are
+// evaluated in the factored form above, and the smallest is taken when it
+// lowers f; when there is none (possible only through rounding of a
+// degenerate ray), the step falls back to backtracking.
+// The joint model of Appendix F weights the tensor term by mu and adds the
+// ratings term, a quartic in alpha with coefficients ycoef[0..4] (nullable).
+// The backtracking trials' values come from gd_ray_values (fvals).
+__global__ void __launch_bounds__(256) gd_line_search(const double* __restrict__ mats, int R,
+                                                     double lambda_reg, double* __restrict__ scal,
+                                                     int32_t* __restrict__ lsfail, int exact,
+                                                     double mu, const double* __restrict__ ycoef,
+                                                     const double* __restrict__ fvals) {
+  __shared__ double red[256];
+  __shared__ double s_q;
+  __shared__ double s_qc[256][7];
+  __shared__ double s_cand[kPolyMax];
+  __shared__ int s_ncand;
+  const int tid = threadIdx.x;
+  const int RR = R * R;
+  const RayObjective obj(mats, R, lambda_reg, scal, mu, ycoef);
+  auto f = [&](double a) { return obj.f(a, red, &s_q); };
+  const double nx2 = obj.nx2, t0 = obj.t0, t1 = obj.t1, t2 = obj.t2, t3 = obj.t3;
+  const double f0 = fvals[0];
   const double g2 = scal[kG2];
   bool ok = false;
   double alpha = 0.0, fa = f0;
@@ -986,7 +1029,7 @@ __global__ void __launch_bounds__(256) gd_line_search(const double* __restrict__
     const double prev = scal[kAlpha];
     alpha = prev > 0.0 ? fmin(2.0 * prev, 1.0) : 1.0;
     for (int trial = 0; trial < kLineSearchTrials; ++trial) {
-      fa = f(alpha);
+      fa = fvals[1 + trial];  // f(alpha), alpha = alpha0 / 2^trial
       if (fa <= f0 - 1e-4 * alpha * g2) {
         ok = true;
         break;
@@ -2383,9 +2426,7 @@ dfacto_status gd_step_rows(dfacto_t* h) {
     DF_CUDA(h, cudaGetLastError());
   }
   if ((st = dual_pass(h)) != DFACTO_OK) return st;
-  gd_line_search<<<1, 256, 0, s>>>(h->gd_mats, R, h->lambda_reg, h->scal, h->flags + kFlagLsFail,
-                                   h->opt.line_search, 1.0, nullptr);
-  DF_COUNT();
+  if ((st = line_search(h, 1.0, nullptr)) != DFACTO_OK) return st;
   for (int m = 0; m < 3; ++m) {
     const int64_t rows = h->dims[m];
     const int nb = pass_blocks(rows);
@@ -2441,9 +2482,7 @@ dfacto_status gd_step_T(dfacto_t* h) {
       return st;
   }
   if ((st = dual_pass(h)) != DFACTO_OK) return st;
-  gd_line_search<<<1, 256, 0, s>>>(h->gd_mats, R, h->lambda_reg, h->scal, h->flags + kFlagLsFail,
-                                   h->opt.line_search, 1.0, nullptr);
-  DF_COUNT();
+  if ((st = line_search(h, 1.0, nullptr)) != DFACTO_OK) return st;
   for (int m = 0; m < 3; ++m) {
     const int64_t n = (int64_t)h->dims[m] * R;
     const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, kMaxBlocks * 4));
@@ -2503,8 +2542,17 @@ dfacto_status ray_matrices(dfacto_t* h) {
 }
 
 dfacto_status line_search(dfacto_t* h, double mu, const double* ycoef) {
+  if (!h->ls_vals) {
+    const dfacto_status st =
+        dalloc(h, reinterpret_cast<void**>(&h->ls_vals), sizeof(double) * (1 + kLineSearchTrials));
+    if (st != DFACTO_OK) return st;
+  }
+  gd_ray_values<<<1 + kLineSearchTrials, 256, 0, h->stream>>>(h->gd_mats, h->R, h->lambda_reg, h->scal,
+                                                             mu, ycoef, h->ls_vals);
+  DF_COUNT();
   gd_line_search<<<1, 256, 0, h->stream>>>(h->gd_mats, h->R, h->lambda_reg, h->scal,
-                                           h->flags + kFlagLsFail, h->opt.line_search, mu, ycoef);
+                                           h->flags + kFlagLsFail, h->opt.line_search, mu, ycoef,
+                                           h->ls_vals);
   DF_COUNT();
   DF_CUDA(h, cudaGetLastError());
   return DFACTO_OK;

@@ -102,6 +102,7 @@ struct dfacto_handle {
   bool gram_valid[3] = {false, false, false};
   double* gd_mats = nullptr;                  // [3 x 3 x R x R] P0/P1/P2 per factor
   uint32_t* gd_scratch = nullptr;             // [8] gradient max bits and scales (dual pass)
+  double* ls_vals = nullptr;                  // [1 + trials] f(0) and the backtracking trials (lazy)
   double* W = nullptr;                        // [R x R] Gamma^{-1} (FP64)
   double* rr_work = nullptr;                  // [2 R^2 + R] workspace of the R x R solve
   float* W32 = nullptr;                       // [R x R] Gamma^{-1} (FP32)
