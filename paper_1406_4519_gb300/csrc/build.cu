@@ -10,10 +10,10 @@
 // The sort is a least-significant-digit radix sort with 8- or 9-bit digits
 // written for this library: per-tile digit histograms, a device-wide scan, and
 // a stable scatter that ranks equal digits inside a warp with
-// __match_any_sync.  Keys
-// of up to 64 bits sort in one run with the nonzero's value as payload; wider
-// (o, f, in) keys take two stable runs (first by `in`, then by (o, f)) with
-// the nonzero's position as payload.
+// __match_any_sync.  Keys of up to 64 bits sort in one run with the nonzero's
+// value as payload; wider (o, f, in) keys take two stable runs (first by `in`,
+// then by (o, f)) with the nonzero's position as payload.  The fiber-end
+// bitmask of the walk comes out of the same pass that flags the fiber starts.
 //
 // The three modes are sorted as a chain m, m + 1, m + 2.  Mode m's sorted
 // order is lexicographic in (m, m + 2, m + 1); mode m + 1 wants
